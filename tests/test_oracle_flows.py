@@ -1,0 +1,86 @@
+"""Flow-level pins for the oracle: the Taylor-Green vortex viscous decay
+exp(-2 nu k^2 t) (2-D) and exp(-3 nu k^2 t) (3-D, wavevector (k,k,k)) with
+nu = cs2 (1/omega - 1/2) (the C_S = 0 limit of the Smagorinsky relation of
+Sec. III-C), and the exact Poiseuille parabola of TRT with Lambda = 3/16 and
+halfway bounce-back under a Guo body force."""
+import numpy as np
+import pytest
+
+from oracle import collision as co
+from oracle import lattice, lbm
+from paper_2001_11806_gb300 import inputs
+
+
+def _amp(u):
+    return np.sqrt((u * u).sum())
+
+
+def test_tgv2d_decay_rate_within_one_percent():
+    n, omega = 64, 1.6
+    lat = lattice.d2q9()
+    s = lbm.Sim(co.Method(lat, "srt", [omega]), (n, n, 1))
+    rho, u = inputs.tgv2d(n, 0.01)
+    s.init_equilibrium(rho, u)
+    ts, amps = [], []
+    for t in range(201):
+        if t >= 20 and t % 10 == 0:
+            ts.append(t)
+            amps.append(_amp(s.macroscopic()[1]))
+        s.step(1)
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    nu = (1 / omega - 0.5) / 3
+    expect = 2 * nu * (2 * np.pi / n) ** 2
+    assert abs(expect - 8.032e-4) < 1e-7
+    assert abs(rate / expect - 1) < 1e-2
+    assert abs(rate / expect - 1) < 1e-4  # measured at 64^2: 1.5e-5
+
+
+def _tgv3d_rate_error(name, op, omegas, n):
+    lat = lattice.get(name)
+    s = lbm.Sim(co.Method(lat, op, omegas), (n, n, n))
+    rho, u = inputs.tgv3d(n, 1e-4)
+    s.init_equilibrium(rho, u)
+    T = int(60 * (n / 16) ** 2)  # same diffusive time at each resolution
+    ts, amps = [], []
+    for t in range(T + 1):
+        if t >= T // 6 and t % (T // 12) == 0:
+            ts.append(t)
+            amps.append(_amp(s.macroscopic()[1]))
+        s.step(1)
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    nu = (1 / omegas[0] - 0.5) / 3
+    return rate / (3 * nu * (2 * np.pi / n) ** 2) - 1
+
+
+@pytest.mark.parametrize("name,op,omegas", [
+    ("D3Q19", "trt", [1.4, 1.4]),
+    ("D3Q19", "mrt", [1.4, 1.0, 1.0, 1.0]),
+    ("D3Q27", "cumulant", [1.4, 1.0, 1.0]),
+])
+def test_tgv3d_low_re_decay_second_order(name, op, omegas):
+    """Decay rate -> 3 nu k^2 with second-order convergence (8^3 -> 16^3)."""
+    e8 = _tgv3d_rate_error(name, op, omegas, 8)
+    e16 = _tgv3d_rate_error(name, op, omegas, 16)
+    assert abs(e16) < 0.05
+    assert 3.5 < e8 / e16 < 5.0, (e8, e16)
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q19"])
+def test_poiseuille_exact_with_magic_trt(name):
+    lat = lattice.get(name)
+    oe = 1.0
+    oo = co.trt_odd_rate(oe, 3 / 16)
+    F = 1e-5
+    H = 8
+    m = co.Method(lat, "trt", [oe, oo], force=[F] + [0.0] * (lat.d - 1))
+    flags = np.zeros((1, H + 2, 1), np.uint8)
+    flags[:, 0, :] = lbm.NOSLIP
+    flags[:, H + 1, :] = lbm.NOSLIP
+    s = lbm.Sim(m, (1, H + 2, 1), periodic=(True, False, True), flags=flags)
+    s.init_equilibrium(np.ones((1, H + 2, 1)), np.zeros((lat.d, 1, H + 2, 1)))
+    s.step(3000)
+    u = s.macroscopic()[1]
+    nu = (1 / oe - 0.5) / 3
+    y = np.arange(1, H + 1)
+    exact = F / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+    assert np.abs(u[0, 0, 1:H + 1, 0] - exact).max() / exact.max() < 1e-10

@@ -1,0 +1,329 @@
+"""Benchmark: D3Q19 TRT FP32 stream-collide sweep on a 256^3 periodic box.
+
+One bench step is one lattice Boltzmann time step (one fused stream-collide
+sweep over all 16.8 M cells, AA in-place pattern).  Synthetic input: 3-D
+Taylor-Green vortex, u0 = 0.02 plus U(-1e-4, 1e-4) noise (SplitMix64 seed 42),
+rho = 1; omega_e = 1.8, Lambda = 3/16.  The population array (1.27 GB) is far
+larger than the 129 MB L2, so no flush is needed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 numpy oracle on the host cores on a bounded
+sample of the same workload (a 32^3 periodic box per step).  Under torchrun
+(N > 1) every rank runs its own replica (weak scaling, no collective on the
+data path); the elapsed time is the maximum over ranks.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 256
+OMEGA_E, MAGIC = 1.8, 3.0 / 16.0
+U0, NOISE, SEED = 0.02, 1e-4, 42
+Q, ELEM = 19, 4
+METRIC = "MLUPS and % of HBM roofline per stencil/collision; FP16/FP32 vs FP64 error"
+WORKLOAD = "D3Q19 TRT FP32 256^3 periodic Taylor-Green vortex, AA in-place pattern"
+REF_SIDE = 32
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2001_11806_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(cells):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_cell"] * cells
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    start() returns only after the first sample has arrived, so that the
+    sampler's own start-up never overlaps the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
+
+    def start(self):
+        import threading
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._reader, daemon=True)
+        self.thread.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 20.0:
+            time.sleep(0.05)
+        self.skip = len(self.lines)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=10)
+        except Exception:
+            self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines[self.skip:]:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_run(steps, warmup, budget_s=None):
+    """The FP64 oracle on a REF_SIDE^3 periodic box of the same workload."""
+    from oracle import collision as oco
+    from oracle import lattice as olat
+    from oracle import lbm as olbm
+    from paper_2001_11806_gb300 import inputs
+    lat = olat.d3q19()
+    sim = olbm.Sim(oco.Method(lat, "trt", [OMEGA_E, oco.trt_odd_rate(OMEGA_E, MAGIC)]), (REF_SIDE,) * 3)
+    rho, u = inputs.tgv3d(REF_SIDE, U0, NOISE, SEED)
+    sim.init_equilibrium(rho, u)
+    sim.step(warmup)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        sim.step(1)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return REF_SIDE ** 3 * done / dt / 1e6, done, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    mlups, done, dt = oracle_sample_run(args.steps, args.warmup)
+    sample = f"FP64 numpy oracle, {REF_SIDE}^3 periodic box of the same TGV workload per step, {done} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / done, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{REF_SIDE}^3 box"},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    from paper_2001_11806_gb300 import inputs
+    from paper_2001_11806_gb300.sim import Sim
+
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    n = args.size
+    cells = n ** 3
+    rho, u = inputs.tgv3d(n, U0, NOISE, SEED)
+    rho_h = torch.from_numpy(rho.reshape(-1)).pin_memory()
+    u_h = torch.from_numpy(u.reshape(3, -1)).pin_memory()
+    stream = torch.cuda.current_stream(device)
+
+    sim = Sim("D3Q19", "trt", "f32", "aa", (n, n, n), omega=[OMEGA_E], trt_magic=MAGIC, device=device)
+    sim.init_equilibrium(rho_h.to(device), u_h.to(device))
+    sim.step(args.warmup)
+    torch.cuda.synchronize(device)
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, ms, device)
+    mlups = cells * args.steps * world / (ms * 1e-3) / 1e6
+    ms_step = ms / args.steps
+
+    # ---- end to end through the public API with host buffers
+    out_rho = torch.empty(cells, dtype=torch.float32).pin_memory()
+    out_u = torch.empty((3, cells), dtype=torch.float32).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rd = rho_h.to(device, non_blocking=True)
+    ud = u_h.to(device, non_blocking=True)
+    sim.init_equilibrium(rd, ud)
+    sim.step(args.steps)
+    r_dev, u_dev = sim.macroscopic(f64=False)
+    out_rho.copy_(r_dev, non_blocking=True)
+    out_u.copy_(u_dev, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(world)
+    e2e_ms = max_over_ranks(world, e0.elapsed_time(e1), device)
+    e2e = {"value": round(cells * args.steps * world / (e2e_ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+           "h2d_bytes_per_step": int((rho_h.numel() + u_h.numel()) * 8 / args.steps),
+           "d2h_bytes_per_step": int((out_rho.numel() + out_u.numel()) * 4 / args.steps)}
+    assert np.isfinite(out_rho.numpy()).all()
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = measured_peak()
+    bytes_per_launch = 2 * Q * ELEM * cells
+    if n != N_SIDE:
+        line_workload = WORKLOAD.replace("256^3", f"{n}^3")
+    else:
+        line_workload = WORKLOAD
+    achieved = bytes_per_launch / (ms_step * 1e-3) / 1e9
+    traffic = recorded_traffic(cells)
+    if args.no_cpu_baseline:
+        cpu_mlups, cpu_steps, cpu_dt = float("nan"), 0, 0.0
+    else:
+        cpu_mlups, cpu_steps, cpu_dt = oracle_sample_run(10 ** 9, 1, budget_s=12.0)
+    line = {
+        "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": line_workload, "stencil": "D3Q19", "collision": "TRT", "omega_e": OMEGA_E,
+                   "magic": MAGIC, "storage": "f32", "pattern": "aa", "cells": cells,
+                   "l2": "inputs larger than L2 (1.27 GB population array vs 129 MB L2)",
+                   "parallelism": f"{world} independent replicas"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "cpu_baseline": {"value": round(cpu_mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 numpy oracle, {REF_SIDE}^3 periodic box of the same workload, "
+                                   f"{cpu_steps} steps in {cpu_dt:.1f} s"},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    # profiling aids: a smaller box of the same kernel, and skipping the CPU leg
+    ap.add_argument("--size", type=int, default=N_SIDE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

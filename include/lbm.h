@@ -1,0 +1,196 @@
+/*
+ * lbm.h -- C ABI of liblbm.so, a GB300 (sm_103a) lattice Boltzmann library.
+ *
+ * The library implements the fused stream-collide sweep of the lattice
+ * Boltzmann method described in Bauer, Koestler & Ruede, "lbmpy: Automatic
+ * code generation for efficient parallel lattice Boltzmann methods"
+ * (arXiv:2001.11806):
+ *   - DdQq stencils D2Q9, D3Q19, D3Q27 (Sec. III-A);
+ *   - macroscopic moments rho = sum f, u = sum c f / rho_0 (Eq. density);
+ *   - second-order discrete equilibrium (Eq. discrete_eq);
+ *   - SRT/BGK (Eq. bgk), TRT (Sec. III-C), MRT with the weighted-orthogonal
+ *     moment basis built from the monomial procedure of Sec. III-A (Eq. mrt),
+ *     cumulant collision for D3Q27 (Sec. III-B, Eq.
+ *     cumulant_generating_function);
+ *   - two-array stream-pull-collide and single-array AA update patterns
+ *     (Sec. IV-B "Streaming and Collision");
+ *   - per-link boundaries compiled into the sweep through a flag field
+ *     (Sec. IV-B "Boundary Conditions"): halfway bounce-back, velocity
+ *     bounce-back (UBB listing of Sec. III-C) and an equilibrium outlet;
+ *   - Guo body forcing (forcing schemes cited in Sec. I);
+ *   - a discrete adjoint of the time step (not in the paper).
+ * Like the generated kernels of Sec. IV-D, every entry point takes raw
+ * pointers, sizes and runtime parameters.
+ *
+ * Conventions
+ *   Cells: x = 0..nx-1 fastest, then y, then z (nz = 1 for D2Q9);
+ *     N = nx*ny*nz, cell index n = x + nx*(y + ny*z).
+ *   Population arrays: structure of arrays [q][N] in the storage type.
+ *   Direction order: 0 is rest; then opposite pairs (2k-1, 2k) as faces
+ *     (+x,-x,+y,-y,+z,-z), edges per axis pair xy, xz, yz with signs
+ *     (+,+),(-,-),(+,-),(-,+), corners (+++,---), (++-,--+), (+-+,-+-),
+ *     (-++,+--).  D2Q9 = rest, 4 faces, 4 xy edges; D3Q19 = rest, faces,
+ *     edges; D3Q27 = D3Q19 + corners.  lbm_stencil_info returns the table.
+ *   State: the library's canonical state P is the post-collision populations
+ *     of the last completed step (two-array pull convention).  A step is
+ *     f_q(x) = P_q(x - c_q) if x - c_q is fluid, else B_q(P(x)) (boundary
+ *     link), then P'(x) = collide(f(x)) on fluid cells.  Initialisation sets
+ *     P = f^eq(rho_0, u_0).  "Populations" are the streamed f of the current
+ *     time; macroscopic output and reductions are moments of them.
+ *   Shifted storage (LBM_F32S, LBM_F16S) stores h_q = f_q - w_q.
+ *
+ * Ownership: the caller allocates and owns every device buffer (for example
+ *   with torch); the library borrows pointers and never frees them.  A
+ *   context owns host metadata only.  Buffers must stay valid until
+ *   lbm_destroy.
+ * Asynchrony: calls enqueue work on the context's CUDA stream and return;
+ *   lbm_reduce and lbm_sync synchronise the stream.
+ * Errors: every call returns lbm_status; none throws, exits or traps.
+ *   Invalid arguments are rejected before any launch.  A CUDA error after a
+ *   launch returns LBM_E_CUDA; lbm_last_error gives the message.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+  LBM_OK = 0,
+  LBM_E_INVAL = 1,       /* bad argument or parameter value */
+  LBM_E_UNSUPPORTED = 2, /* valid but not built (e.g. cumulant on D2Q9) */
+  LBM_E_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  LBM_E_NOMEM = 4,       /* host allocation failed */
+  LBM_E_BUFSIZE = 5,     /* a caller buffer is smaller than required */
+  LBM_E_NONFINITE = 6,   /* a reduction found NaN or Inf */
+  LBM_E_BOUNDS = 7,      /* reserved: out-of-bounds index caught by a debug build */
+  LBM_E_STATE = 8        /* call not valid in the current state */
+} lbm_status;
+
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
+enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2, LBM_CUMULANT = 3 };
+/* storage type of the population arrays; the collision computes in FP64 for
+ * LBM_F64 and in FP32 for the others */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F32S = 3 };
+enum { LBM_PULL = 0, LBM_AA = 1 };
+/* uint8 flag per cell; 0 = fluid.  A boundary link (x, q) takes its type from
+ * the flag of its source cell x - c_q with precedence NOSLIP > INLET > OUTLET
+ * (a non-zero flag with none of these bits counts as NOSLIP).  Sources outside
+ * a non-periodic axis count as NOSLIP. */
+enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_INLET = 2, LBM_OUTLET = 4 };
+/* bit 31 of a link-mask word marks a non-fluid cell; bit 30 marks a fluid
+ * cell that has at least one INLET or OUTLET link */
+#define LBM_MASK_SOLID 0x80000000u
+#define LBM_MASK_SPECIAL 0x40000000u
+
+typedef struct lbm_params {
+  int32_t stencil;      /* LBM_D2Q9 | LBM_D3Q19 | LBM_D3Q27 */
+  int32_t collision;    /* LBM_SRT | LBM_TRT | LBM_MRT | LBM_CUMULANT */
+  int32_t storage;      /* LBM_F64 | LBM_F32 | LBM_F16S | LBM_F32S */
+  int32_t pattern;      /* LBM_PULL | LBM_AA */
+  int32_t nx, ny, nz;   /* nz must be 1 for D2Q9; each >= 1 */
+  int32_t periodic[3];  /* non-zero = periodic along x, y, z */
+  /* relaxation rates, each in (0, 2):
+   *   SRT: omega[0] = omega.
+   *   TRT: omega[0] = omega_e (even moments), omega[1] = omega_o (odd).
+   *   MRT: shear, bulk, 3rd-order, 4th-order, 5th-order, 6th-order rates
+   *        (orders 5 and 6 exist for D3Q27 only); conserved moments use 0.
+   *   CUMULANT: shear, bulk, higher-order (orders >= 3). */
+  double omega[6];
+  int32_t trt_magic;    /* TRT: non-zero derives omega_o from omega_e and Lambda = magic */
+  int32_t incompressible; /* non-zero: rho_0 = 1 in velocity terms (Sec. III-A) */
+  double magic;         /* Lambda = (1/omega_e - 1/2)(1/omega_o - 1/2), e.g. 3/16 */
+  double u_wall[3];     /* velocity of INLET (UBB) links, rho_0 = 1 */
+  double rho_outlet;    /* density of OUTLET links: B_q = f^eq_q(rho_outlet, u_P(x)) */
+  double force[3];      /* uniform body force, Guo scheme; zero = no force */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *p with defaults: D3Q19 TRT FP32 pull, 1^3 periodic cells, omega 1.0,
+ * rho_outlet 1, no force. */
+void lbm_default_params(lbm_params* p);
+
+/* Stencil table: *q, *d, and if non-NULL c[q*3] (integer velocities, unused
+ * components zero) and w[q] (weights).  Returns LBM_E_INVAL for an unknown
+ * stencil. */
+lbm_status lbm_stencil_info(int32_t stencil, int32_t* q, int32_t* d, int32_t* c, double* w);
+
+/* Bytes the caller must allocate: pdf_bytes for each population array
+ * (q * N * sizeof(storage)); aux_bytes for the auxiliary device buffer
+ * (link mask of 4*N bytes when flags or non-periodic axes are used, plus the
+ * reduction scratch).  Validates p. */
+lbm_status lbm_query_sizes(const lbm_params* p, size_t* pdf_bytes, size_t* aux_bytes);
+
+/* Create a context over caller-owned device buffers.
+ *   pdf, pdf2: population arrays of pdf_bytes each; pdf2 must be non-NULL for
+ *     LBM_PULL and is ignored (may be NULL) for LBM_AA.
+ *   aux: auxiliary device buffer of aux_bytes.
+ *   flags: device uint8[N] flag field or NULL (all fluid).  It is read at
+ *     creation (to build the link mask) and on boundary links during steps.
+ *   stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Byte sizes are checked against lbm_query_sizes (LBM_E_BUFSIZE).  The
+ * populations are undefined until lbm_init_equilibrium or lbm_set_state. */
+lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_bytes,
+                      void* pdf2, size_t pdf2_bytes, void* aux, size_t aux_bytes,
+                      const uint8_t* flags, void* stream);
+
+/* Change the stream later calls enqueue on. */
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Set P = f^eq(rho_0, u_0) (Eq. discrete_eq) from device FP64 arrays
+ * rho[N] and u[d][N]; resets the step counter to 0. */
+lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u);
+
+/* Set P from a device FP64 array P[q][N] (unshifted populations); resets
+ * the step counter to 0. */
+lbm_status lbm_set_state(lbm_ctx* ctx, const double* P);
+
+/* Advance n >= 0 time steps (asynchronous). */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
+
+/* Number of steps since the last initialisation (AA parity = t mod 2). */
+lbm_status lbm_get_time(const lbm_ctx* ctx, int64_t* t);
+
+/* Populations f of the current time (streamed, pre-collision, unshifted) as
+ * device FP64 f[q][N]; non-fluid cells are written as NaN. */
+lbm_status lbm_populations(lbm_ctx* ctx, double* f);
+
+/* rho[N] and u[d][N] (device, FP64 if out_f64 else FP32) from the current
+ * populations: rho = sum f, u = (sum c f + F/2) / rho_0 (Eq. density with the
+ * Guo half force).  Non-fluid cells are written as NaN. */
+lbm_status lbm_macroscopic(lbm_ctx* ctx, void* rho, void* u, int32_t out_f64);
+
+/* FP64 sums over fluid cells: out[0] = sum rho, out[1..3] = sum rho_0 u,
+ * out[4] = (1/2) sum rho |u|^2.  Host array out[5].  Synchronises the
+ * stream.  Returns LBM_E_NONFINITE if any sum is NaN or Inf. */
+lbm_status lbm_reduce(lbm_ctx* ctx, double out[5]);
+
+/* Raw copy of the native population storage (pdf_bytes, device to device),
+ * for checkpoint/restore.  lbm_set_pdfs also sets the step counter to t so
+ * that the AA parity matches the saved data. */
+lbm_status lbm_get_pdfs(lbm_ctx* ctx, void* dst);
+lbm_status lbm_set_pdfs(lbm_ctx* ctx, const void* src, int64_t t);
+
+/* Device uint32[N] link mask: bit q set when the source x - c_q of a fluid
+ * cell x is not fluid (a boundary link); LBM_MASK_SPECIAL when one of those
+ * links is an INLET or OUTLET link; LBM_MASK_SOLID for non-fluid cells.
+ * Computed on the device from the flags. */
+lbm_status lbm_link_mask(lbm_ctx* ctx, uint32_t* mask);
+
+/* Block until the context's stream is idle; maps pending CUDA errors. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+const char* lbm_status_str(lbm_status s);
+/* Last error message of this context ("" if none); never NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -23,7 +23,8 @@ Output.  ``populations`` returns f(x) (the pre-collision populations the next
 step would collide); ``macroscopic`` returns their moments (Eq. density, with
 the Guo half-force); ``reduce`` returns sum rho, sum rho_0 u and
 (1/2) sum rho |u|^2 over fluid cells; ``link_mask`` sets bit q for every
-boundary link (x, q) of a fluid cell and bit 31 for non-fluid cells.
+boundary link (x, q) of a fluid cell, bit 30 for a fluid cell with an INLET
+or OUTLET link and bit 31 for non-fluid cells.
 
 Pins: tests/test_oracle_lbm.py (pull streaming against an independent
 np.roll shift, global mass conservation with walls, bounce-back reversing a
@@ -107,9 +108,12 @@ class Sim:
 
     def link_mask(self):
         mask = np.zeros(self.shape3, dtype=np.uint64)
+        special = np.zeros(self.shape3, dtype=bool)
         for q in range(self.lat.q):
             b = (self.kind[q] != FLUID) & self.fluid
             mask |= b.astype(np.uint64) << np.uint64(q)
+            special |= self.fluid & ((self.kind[q] == INLET) | (self.kind[q] == OUTLET))
+        mask |= special.astype(np.uint64) << np.uint64(30)
         mask |= (~self.fluid).astype(np.uint64) << np.uint64(31)
         return mask.astype(np.uint32)
 

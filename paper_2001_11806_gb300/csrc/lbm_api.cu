@@ -1,0 +1,430 @@
+// C ABI of liblbm.so (declared in include/lbm.h): validation, buffer
+// bookkeeping and dispatch to the kernels instantiated per stencil/storage.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+__global__ void k_reduce_final(const double* partials, int nblocks, double* out) {
+  if (threadIdx.x < 5) {
+    double s = 0;
+    for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+OpsTable get_table(int stencil, int storage) {
+  switch (stencil * 4 + storage) {
+    case LBM_D2Q9 * 4 + LBM_F64: return ops_table_d2q9_f64();
+    case LBM_D2Q9 * 4 + LBM_F32: return ops_table_d2q9_f32();
+    case LBM_D2Q9 * 4 + LBM_F16S: return ops_table_d2q9_f16s();
+    case LBM_D2Q9 * 4 + LBM_F32S: return ops_table_d2q9_f32s();
+    case LBM_D3Q19 * 4 + LBM_F64: return ops_table_d3q19_f64();
+    case LBM_D3Q19 * 4 + LBM_F32: return ops_table_d3q19_f32();
+    case LBM_D3Q19 * 4 + LBM_F16S: return ops_table_d3q19_f16s();
+    case LBM_D3Q19 * 4 + LBM_F32S: return ops_table_d3q19_f32s();
+    case LBM_D3Q27 * 4 + LBM_F64: return ops_table_d3q27_f64();
+    case LBM_D3Q27 * 4 + LBM_F32: return ops_table_d3q27_f32();
+    case LBM_D3Q27 * 4 + LBM_F16S: return ops_table_d3q27_f16s();
+    default: return ops_table_d3q27_f32s();
+  }
+}
+
+template <class L>
+void mrt_factors(const double* omega, CollideParams& cp) {
+  constexpr auto& B = mrt::Table<L>::B;
+  for (int k = 0; k < 27; ++k) { cp.mrt_s[k] = 0.f; cp.mrt_s_d[k] = 0.0; }
+  for (int k = 0; k < L::Q; ++k) {
+    const double s = B.group[k] < 0 ? 0.0 : omega[B.group[k]];
+    cp.mrt_s_d[k] = s * B.invD[k];
+    cp.mrt_s[k] = (float)cp.mrt_s_d[k];
+  }
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+  lbm_params p;
+  int q = 0, d = 0;
+  long long N = 0;
+  size_t elem = 0, pdf_bytes = 0, aux_bytes = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;  // pull: index of the buffer that holds P
+  void* aux = nullptr;
+  const uint8_t* flags = nullptr;
+  uint32_t* mask = nullptr;
+  double* partials = nullptr;
+  double* result = nullptr;
+  bool has_mask = false;
+  cudaStream_t stream = nullptr;
+  int64_t t = 0;
+  CollideParams cp;
+  OpsTable ops;
+  std::string err;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"LBM_OK", "LBM_E_INVAL", "LBM_E_UNSUPPORTED", "LBM_E_CUDA", "LBM_E_NOMEM",
+                              "LBM_E_BUFSIZE", "LBM_E_NONFINITE", "LBM_E_BOUNDS", "LBM_E_STATE"};
+
+struct Layout {
+  size_t mask_off, mask_bytes, part_off, res_off, total;
+};
+
+int stencil_q(int s) { return s == LBM_D2Q9 ? 9 : (s == LBM_D3Q19 ? 19 : 27); }
+int stencil_d(int s) { return s == LBM_D2Q9 ? 2 : 3; }
+size_t storage_bytes(int st) { return st == LBM_F64 ? 8 : (st == LBM_F16S ? 2 : 4); }
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+bool needs_mask(const lbm_params& p, bool has_flags) {
+  if (has_flags) return true;
+  const int d = stencil_d(p.stencil);
+  for (int a = 0; a < d; ++a)
+    if (!p.periodic[a]) return true;
+  return false;
+}
+
+// aux = [link mask: 4 N bytes][reduction partials][reduction result]; the
+// mask region is always reserved so that the size does not depend on flags.
+Layout layout_for(const lbm_params& p, long long N) {
+  Layout l;
+  l.mask_off = 0;
+  l.mask_bytes = align256(size_t(N) * 4);
+  l.part_off = l.mask_bytes;
+  l.res_off = l.part_off + align256(size_t(kRedMaxBlocks) * 5 * sizeof(double));
+  l.total = l.res_off + 256;
+  return l;
+}
+
+bool rate_ok(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
+
+// Validate parameters; fills msg on failure.
+lbm_status validate(const lbm_params* p, std::string* msg) {
+  if (!p) { *msg = "params is NULL"; return LBM_E_INVAL; }
+  if (p->stencil < LBM_D2Q9 || p->stencil > LBM_D3Q27) { *msg = "unknown stencil"; return LBM_E_INVAL; }
+  if (p->collision < LBM_SRT || p->collision > LBM_CUMULANT) { *msg = "unknown collision"; return LBM_E_INVAL; }
+  if (p->storage < LBM_F64 || p->storage > LBM_F32S) { *msg = "unknown storage"; return LBM_E_INVAL; }
+  if (p->pattern != LBM_PULL && p->pattern != LBM_AA) { *msg = "unknown pattern"; return LBM_E_INVAL; }
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) { *msg = "nx, ny, nz must be >= 1"; return LBM_E_INVAL; }
+  if (p->stencil == LBM_D2Q9 && p->nz != 1) { *msg = "D2Q9 needs nz == 1"; return LBM_E_INVAL; }
+  if (p->ny > 65535 || p->nz > 65535) { *msg = "ny and nz must be <= 65535"; return LBM_E_INVAL; }
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > 2147483647LL) { *msg = "more than 2^31-1 cells"; return LBM_E_INVAL; }
+  switch (p->collision) {
+    case LBM_SRT:
+      if (!rate_ok(p->omega[0])) { *msg = "omega[0] must be in (0, 2)"; return LBM_E_INVAL; }
+      break;
+    case LBM_TRT:
+      if (!rate_ok(p->omega[0])) { *msg = "omega_e must be in (0, 2)"; return LBM_E_INVAL; }
+      if (p->trt_magic) {
+        if (!(p->magic > 0.0) || !std::isfinite(p->magic)) { *msg = "magic must be > 0"; return LBM_E_INVAL; }
+      } else if (!rate_ok(p->omega[1])) {
+        *msg = "omega_o must be in (0, 2)";
+        return LBM_E_INVAL;
+      }
+      break;
+    case LBM_MRT: {
+      const int nr = p->stencil == LBM_D3Q27 ? 6 : 4;
+      for (int i = 0; i < nr; ++i)
+        if (!rate_ok(p->omega[i])) { *msg = "MRT rates must be in (0, 2)"; return LBM_E_INVAL; }
+      break;
+    }
+    case LBM_CUMULANT:
+      for (int i = 0; i < 3; ++i)
+        if (!rate_ok(p->omega[i])) { *msg = "cumulant rates must be in (0, 2)"; return LBM_E_INVAL; }
+      if (p->stencil != LBM_D3Q27) { *msg = "the cumulant operator is built for D3Q27 only"; return LBM_E_UNSUPPORTED; }
+      if (p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0) {
+        *msg = "cumulant collision with a body force is not built";
+        return LBM_E_UNSUPPORTED;
+      }
+      if (p->incompressible) { *msg = "incompressible cumulant collision is not built"; return LBM_E_UNSUPPORTED; }
+      break;
+  }
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p->force[i]) || !std::isfinite(p->u_wall[i])) { *msg = "non-finite force or wall velocity"; return LBM_E_INVAL; }
+  if (!(p->rho_outlet > 0.0) || !std::isfinite(p->rho_outlet)) { *msg = "rho_outlet must be > 0"; return LBM_E_INVAL; }
+  return LBM_OK;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return LBM_E_CUDA;
+}
+
+SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
+  SweepArgs a;
+  a.src = src;
+  a.dst = dst;
+  a.mask = c->has_mask ? c->mask : nullptr;
+  a.flags = c->flags;
+  a.g.nx = c->p.nx;
+  a.g.ny = c->p.ny;
+  a.g.nz = c->p.nz;
+  for (int i = 0; i < 3; ++i) a.g.per[i] = c->p.periodic[i] ? 1 : 0;
+  if (c->d == 2) a.g.per[2] = 1;
+  a.g.N = c->N;
+  a.cp = c->cp;
+  for (int q = 0; q < 27; ++q) {
+    const size_t off = q < c->q ? size_t(q) * size_t(c->N) * c->elem : 0;
+    a.srcq[q] = src ? static_cast<const char*>(src) + off : nullptr;
+    a.dstq[q] = dst ? static_cast<char*>(dst) + off : nullptr;
+  }
+  return a;
+}
+
+int current_view(const lbm_ctx* c) {
+  if (c->p.pattern == LBM_PULL) return V_PULL;
+  return (c->t & 1) ? V_AA_INVERTED : V_AA_NATURAL;
+}
+
+void fill_collide_params(lbm_ctx* c) {
+  const lbm_params& p = c->p;
+  CollideParams& cp = c->cp;
+  std::memset(&cp, 0, sizeof(cp));
+  double om[6];
+  for (int i = 0; i < 6; ++i) om[i] = p.omega[i];
+  if (p.collision == LBM_TRT && p.trt_magic) om[1] = 1.0 / (p.magic / (1.0 / om[0] - 0.5) + 0.5);
+  if (p.collision == LBM_MRT && p.stencil != LBM_D3Q27) { om[4] = 1.0; om[5] = 1.0; }
+  for (int i = 0; i < 6; ++i) { cp.om_d[i] = om[i]; cp.om[i] = (float)om[i]; }
+  if (p.collision == LBM_MRT) {
+    if (p.stencil == LBM_D2Q9) mrt_factors<D2Q9>(om, cp);
+    else if (p.stencil == LBM_D3Q19) mrt_factors<D3Q19>(om, cp);
+    else mrt_factors<D3Q27>(om, cp);
+  }
+  cp.has_force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;
+  for (int i = 0; i < 3; ++i) { cp.F[i] = p.force[i]; cp.u_wall[i] = p.u_wall[i]; }
+  if (c->d == 2) { cp.F[2] = 0.0; cp.u_wall[2] = 0.0; }
+  cp.incompressible = p.incompressible ? 1 : 0;
+  cp.rho_out = p.rho_outlet;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->stencil = LBM_D3Q19;
+  p->collision = LBM_TRT;
+  p->storage = LBM_F32;
+  p->pattern = LBM_PULL;
+  p->nx = p->ny = p->nz = 1;
+  p->periodic[0] = p->periodic[1] = p->periodic[2] = 1;
+  for (int i = 0; i < 6; ++i) p->omega[i] = 1.0;
+  p->magic = 3.0 / 16.0;
+  p->rho_outlet = 1.0;
+}
+
+lbm_status lbm_stencil_info(int32_t stencil, int32_t* q, int32_t* d, int32_t* c, double* w) {
+  if (stencil < LBM_D2Q9 || stencil > LBM_D3Q27) return LBM_E_INVAL;
+  const int Q = stencil_q(stencil);
+  if (q) *q = Q;
+  if (d) *d = stencil_d(stencil);
+  for (int k = 0; k < Q; ++k) {
+    int cx, cy, cz;
+    double wk;
+    if (stencil == LBM_D2Q9) { cx = D2Q9::cx(k); cy = D2Q9::cy(k); cz = 0; wk = D2Q9::w(k); }
+    else if (stencil == LBM_D3Q19) { cx = D3Q19::cx(k); cy = D3Q19::cy(k); cz = D3Q19::cz(k); wk = D3Q19::w(k); }
+    else { cx = D3Q27::cx(k); cy = D3Q27::cy(k); cz = D3Q27::cz(k); wk = D3Q27::w(k); }
+    if (c) { c[3 * k] = cx; c[3 * k + 1] = cy; c[3 * k + 2] = cz; }
+    if (w) w[k] = wk;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_query_sizes(const lbm_params* p, size_t* pdf_bytes, size_t* aux_bytes) {
+  std::string msg;
+  const lbm_status s = validate(p, &msg);
+  if (s != LBM_OK) return s;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (pdf_bytes) *pdf_bytes = size_t(stencil_q(p->stencil)) * size_t(N) * storage_bytes(p->storage);
+  if (aux_bytes) *aux_bytes = layout_for(*p, N).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_bytes, void* pdf2,
+                      size_t pdf2_bytes, void* aux, size_t aux_bytes, const uint8_t* flags, void* stream) {
+  if (!out) return LBM_E_INVAL;
+  *out = nullptr;
+  std::string msg;
+  lbm_status s = validate(p, &msg);
+  if (s != LBM_OK) return s;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const size_t need = size_t(stencil_q(p->stencil)) * size_t(N) * storage_bytes(p->storage);
+  const bool mask = needs_mask(*p, flags != nullptr);
+  const Layout lay = layout_for(*p, N);
+  if (!pdf || !aux) return LBM_E_INVAL;
+  if (p->pattern == LBM_PULL && !pdf2) return LBM_E_INVAL;
+  if (pdf_bytes < need || (p->pattern == LBM_PULL && pdf2_bytes < need) || aux_bytes < lay.total)
+    return LBM_E_BUFSIZE;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx;
+  if (!c) return LBM_E_NOMEM;
+  c->p = *p;
+  c->q = stencil_q(p->stencil);
+  c->d = stencil_d(p->stencil);
+  c->N = N;
+  c->elem = storage_bytes(p->storage);
+  c->pdf_bytes = need;
+  c->aux_bytes = aux_bytes;
+  c->buf[0] = pdf;
+  c->buf[1] = p->pattern == LBM_PULL ? pdf2 : pdf;
+  c->aux = aux;
+  c->flags = flags;
+  c->has_mask = mask;
+  c->mask = mask ? reinterpret_cast<uint32_t*>(static_cast<char*>(aux) + lay.mask_off) : nullptr;
+  c->partials = reinterpret_cast<double*>(static_cast<char*>(aux) + lay.part_off);
+  c->result = reinterpret_cast<double*>(static_cast<char*>(aux) + lay.res_off);
+  c->stream = static_cast<cudaStream_t>(stream);
+  fill_collide_params(c);
+  c->ops = get_table(p->stencil, p->storage);
+  if (mask) {
+    SweepArgs a = make_args(c, nullptr, nullptr);
+    cudaError_t e = c->ops.link_mask(a, c->mask, c->stream);
+    if (e != cudaSuccess) {
+      delete c;
+      return LBM_E_CUDA;
+    }
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (!c) return LBM_E_INVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) {
+  if (!c || !rho || !u) return LBM_E_INVAL;
+  c->cur = 0;
+  SweepArgs a = make_args(c, nullptr, c->buf[0]);
+  cudaError_t e = c->ops.set_state(c->p.pattern == LBM_AA, 1, a, nullptr, rho, u, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init_equilibrium");
+  c->t = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const double* P) {
+  if (!c || !P) return LBM_E_INVAL;
+  c->cur = 0;
+  SweepArgs a = make_args(c, nullptr, c->buf[0]);
+  cudaError_t e = c->ops.set_state(c->p.pattern == LBM_AA, 0, a, P, nullptr, nullptr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+  c->t = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int32_t n) {
+  if (!c || n < 0) return LBM_E_INVAL;
+  for (int32_t i = 0; i < n; ++i) {
+    cudaError_t e;
+    if (c->p.pattern == LBM_PULL) {
+      SweepArgs a = make_args(c, c->buf[c->cur], c->buf[1 - c->cur]);
+      e = c->ops.sweep(c->p.collision, K_PULL, c->has_mask, a, c->stream);
+      if (e == cudaSuccess) c->cur = 1 - c->cur;
+    } else {
+      SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
+      e = c->ops.sweep(c->p.collision, (c->t & 1) ? K_AA_ODD : K_AA_EVEN, c->has_mask, a, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "step");
+    ++c->t;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_time(const lbm_ctx* c, int64_t* t) {
+  if (!c || !t) return LBM_E_INVAL;
+  *t = c->t;
+  return LBM_OK;
+}
+
+lbm_status lbm_populations(lbm_ctx* c, double* f) {
+  if (!c || !f) return LBM_E_INVAL;
+  SweepArgs a = make_args(c, c->buf[c->cur], nullptr);
+  cudaError_t e = c->ops.populations(current_view(c), a, f, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "populations");
+}
+
+lbm_status lbm_macroscopic(lbm_ctx* c, void* rho, void* u, int32_t out_f64) {
+  if (!c || !rho || !u) return LBM_E_INVAL;
+  SweepArgs a = make_args(c, c->buf[c->cur], nullptr);
+  cudaError_t e = c->ops.macroscopic(current_view(c), a, rho, u, out_f64 != 0, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "macroscopic");
+}
+
+lbm_status lbm_reduce(lbm_ctx* c, double out[5]) {
+  if (!c || !out) return LBM_E_INVAL;
+  SweepArgs a = make_args(c, c->buf[c->cur], nullptr);
+  int nb = grid_stride_blocks(c->N, kRedThreads);
+  if (nb > kRedMaxBlocks) nb = kRedMaxBlocks;
+  cudaError_t e = c->ops.reduce_partial(current_view(c), a, c->partials, nb, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce");
+  k_reduce_final<<<1, 32, 0, c->stream>>>(c->partials, nb, c->result);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce");
+  e = cudaMemcpyAsync(out, c->result, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce copy");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce sync");
+  for (int i = 0; i < 5; ++i)
+    if (!std::isfinite(out[i])) {
+      c->err = "reduction produced a non-finite value";
+      return LBM_E_NONFINITE;
+    }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_pdfs(lbm_ctx* c, void* dst) {
+  if (!c || !dst) return LBM_E_INVAL;
+  cudaError_t e = cudaMemcpyAsync(dst, c->buf[c->cur], c->pdf_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "get_pdfs");
+}
+
+lbm_status lbm_set_pdfs(lbm_ctx* c, const void* src, int64_t t) {
+  if (!c || !src || t < 0) return LBM_E_INVAL;
+  cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], src, c->pdf_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_pdfs");
+  c->t = t;
+  return LBM_OK;
+}
+
+lbm_status lbm_link_mask(lbm_ctx* c, uint32_t* mask) {
+  if (!c || !mask) return LBM_E_INVAL;
+  cudaError_t e;
+  if (c->has_mask) {
+    e = cudaMemcpyAsync(mask, c->mask, size_t(c->N) * 4, cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    e = cudaMemsetAsync(mask, 0, size_t(c->N) * 4, c->stream);
+  }
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "link_mask");
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "sync");
+}
+
+const char* lbm_status_str(lbm_status s) {
+  if ((int)s < 0 || (int)s > 8) return "LBM_E_UNKNOWN";
+  return kStatusNames[(int)s];
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : ""; }
+
+void lbm_destroy(lbm_ctx* c) { delete c; }
+
+}  // extern "C"

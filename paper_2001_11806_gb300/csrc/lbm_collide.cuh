@@ -1,0 +1,270 @@
+// Per-cell collision operators, computed in registers on shifted populations
+// h_q = f_q - w_q (so rho - 1 = sum h is accurate in FP32).
+//
+//   Eq. density: rho = sum f, u = (sum c f + F/2) / rho_0 (rho_0 = rho, or 1
+//     for the incompressible variant of Sec. III-A; F/2 is the Guo half force).
+//   Eq. discrete_eq (second order):
+//     h^eq_q = w_q [ (rho - 1) + rho_0 (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ].
+//   Guo source: G_q = w_q [3 (c_q - u).F + 9 (c_q.u)(c_q.F)].
+//   With g = h - h^eq + G/2 every operator is h* = h + G - R g:
+//     SRT  (Eq. bgk):  R = omega I;
+//     TRT  (Sec. III-C): R = omega_e on the even part, omega_o on the odd part
+//          of each opposite pair;
+//     MRT  (Eq. mrt):  R = M^-1 S M = W M^T D^-1 S M for the w-orthogonal
+//          basis of lbm_mrt.cuh.
+//   The cumulant operator (Sec. III-B) is in lbm_cumulant.cuh.
+#pragma once
+#include <utility>
+
+#include "lbm_lattice.cuh"
+#include "lbm_mrt.cuh"
+
+namespace lbm {
+
+enum Op : int { OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3 };
+
+// Runtime parameters of a sweep, passed by value to the kernel.
+struct CollideParams {
+  float om[6];          // FP32 copies of the rates (see rates_d for FP64)
+  double om_d[6];
+  float mrt_s[27];      // s_k / D_k per MRT moment, FP32
+  double mrt_s_d[27];   // s_k / D_k per MRT moment, FP64
+  double F[3];          // body force
+  int has_force;
+  int incompressible;
+  double u_wall[3];
+  double rho_out;
+};
+
+template <class T> __device__ __forceinline__ T rate(const CollideParams& p, int i);
+template <> __device__ __forceinline__ float rate<float>(const CollideParams& p, int i) { return p.om[i]; }
+template <> __device__ __forceinline__ double rate<double>(const CollideParams& p, int i) { return p.om_d[i]; }
+template <class T> __device__ __forceinline__ T mrt_factor(const CollideParams& p, int k);
+template <> __device__ __forceinline__ float mrt_factor<float>(const CollideParams& p, int k) { return p.mrt_s[k]; }
+template <> __device__ __forceinline__ double mrt_factor<double>(const CollideParams& p, int k) { return p.mrt_s_d[k]; }
+
+template <class L, class T>
+struct Macro {
+  T drho;   // rho - 1
+  T rho0;   // rho (compressible) or 1
+  T u[3];
+  T F[3];
+};
+
+template <class L, class T>
+__device__ __forceinline__ Macro<L, T> macro_from_h(const T (&h)[L::Q], const CollideParams& p) {
+  Macro<L, T> m;
+  T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    drho += h[q];
+    if (L::cx(q) == 1) jx += h[q];
+    if (L::cx(q) == -1) jx -= h[q];
+    if (L::cy(q) == 1) jy += h[q];
+    if (L::cy(q) == -1) jy -= h[q];
+    if (L::cz(q) == 1) jz += h[q];
+    if (L::cz(q) == -1) jz -= h[q];
+  }
+  m.F[0] = m.F[1] = m.F[2] = T(0);
+  if (p.has_force) {
+    m.F[0] = T(p.F[0]); m.F[1] = T(p.F[1]); m.F[2] = T(p.F[2]);
+    jx += T(0.5) * m.F[0]; jy += T(0.5) * m.F[1]; jz += T(0.5) * m.F[2];
+  }
+  m.drho = drho;
+  m.rho0 = p.incompressible ? T(1) : T(1) + drho;
+  T inv = T(1) / m.rho0;
+  m.u[0] = jx * inv; m.u[1] = jy * inv; m.u[2] = L::D == 3 ? jz * inv : T(0);
+  return m;
+}
+
+// c_q . v for a small vector v.
+template <class L, class T>
+__device__ __forceinline__ T cdot(int q, const T (&v)[3]) {
+  T r = T(0);
+  if (L::cx(q) == 1) r += v[0];
+  if (L::cx(q) == -1) r -= v[0];
+  if (L::cy(q) == 1) r += v[1];
+  if (L::cy(q) == -1) r -= v[1];
+  if (L::D == 3) {
+    if (L::cz(q) == 1) r += v[2];
+    if (L::cz(q) == -1) r -= v[2];
+  }
+  return r;
+}
+
+// Even and odd parts of h^eq for direction q (q and opp(q) share them).
+template <class L, class T>
+__device__ __forceinline__ void heq_parts(int q, const Macro<L, T>& m, T usq15, T& even, T& odd) {
+  const T w = T(L::w(q));
+  const T cu = cdot<L, T>(q, m.u);
+  even = w * (m.drho + m.rho0 * (T(4.5) * cu * cu - usq15));
+  odd = w * m.rho0 * T(3) * cu;
+}
+
+// Guo source split into even and odd parts for direction q.
+template <class L, class T>
+__device__ __forceinline__ void guo_parts(int q, const Macro<L, T>& m, T uF3, T& even, T& odd) {
+  const T w = T(L::w(q));
+  const T cF = cdot<L, T>(q, m.F);
+  const T cu = cdot<L, T>(q, m.u);
+  even = w * (T(9) * cu * cF - uF3);
+  odd = w * T(3) * cF;
+}
+
+// ---------------------------------------------------------------- SRT / TRT
+// Pair form.  For each opposite pair (q, qbar) let s = h_q + h_qbar and
+// d = h_q - h_qbar (h = f - w); then (TRT, Sec. III-C)
+//   h*_q    = A + B,  h*_qbar = A - B,
+//   A = (1 - omega_e) s/2 + omega_e h^eq+_q + (1 - omega_e/2) G+_q,
+//   B = (1 - omega_o) d/2 + omega_o h^eq-_q + (1 - omega_o/2) G-_q,
+//   h^eq+_q = w_q ((rho - 1) + rho_0 (9/2 (c.u)^2 - 3/2 u.u)),
+//   h^eq-_q = 3 w_q rho_0 c.u,
+// and SRT (Eq. bgk) is omega_o = omega_e.  rho and j come from the same s and
+// d.  With unshifted storage (DH = false) the registers hold f: the pair sums
+// are shifted by 2 w_q on the fly and w_q is added back once to each result,
+// so the arithmetic, and its rounding, is that of the shifted form.
+template <class T>
+__device__ __forceinline__ void acc_signed(T& acc, bool& init, int sign, T x) {
+  if (sign == 0) return;
+  if (!init) { acc = sign > 0 ? x : -x; init = true; }
+  else acc = sign > 0 ? acc + x : acc - x;
+}
+
+template <class L, class T, int OP, bool DH>
+__device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams& p) {
+  constexpr int NP = (L::Q - 1) / 2;
+  T s[NP], d[NP];
+  const T h0 = DH ? v[0] : v[0] - T(L::w(0));
+  T drho = h0;
+  T jx = T(0), jy = T(0), jz = T(0);
+  bool ix = false, iy = false, iz = false;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    s[k] = DH ? v[q] + v[q + 1] : (v[q] + v[q + 1]) - T(2.0 * L::w(q));
+    d[k] = v[q] - v[q + 1];
+    drho += s[k];
+    acc_signed(jx, ix, L::cx(q), d[k]);
+    acc_signed(jy, iy, L::cy(q), d[k]);
+    acc_signed(jz, iz, L::cz(q), d[k]);
+  }
+  T F[3] = {T(0), T(0), T(0)};
+  const bool force = p.has_force != 0;
+  if (force) {
+    F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
+    jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
+  }
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
+  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T base = drho - T(1.5) * rho0 * usq;
+  const T k45 = T(4.5) * rho0;
+  const T oe = rate<T>(p, 0);
+  const T oo = OP == OP_SRT ? oe : rate<T>(p, 1);
+  const T c1 = T(0.5) - T(0.5) * oe, c2 = T(0.5) - T(0.5) * oo;
+  const T m3o = T(3) * rho0 * oo;
+  const T ge = T(1) - T(0.5) * oe, go = T(1) - T(0.5) * oo;
+  const T uF3 = T(3) * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
+  {
+    T r0 = h0 - oe * (h0 - T(L::w(0)) * base);
+    if (force) r0 -= ge * T(L::w(0)) * uF3;
+    v[0] = DH ? r0 : T(L::w(0)) + r0;
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    T A = fma(c1, s[k], (oe * w) * fma(k45, cu * cu, base));
+    T B = fma(c2, d[k], (m3o * w) * cu);
+    if (force) {
+      const T cF = cdot<L, T>(q, F);
+      A += ge * w * (T(9) * cu * cF - uF3);
+      B += go * w * T(3) * cF;
+    }
+    v[q] = DH ? A + B : w + (A + B);
+    v[q + 1] = DH ? A - B : w + (A - B);
+  }
+}
+
+// ---------------------------------------------------------------------- MRT
+// compile-time entries of the basis table
+template <class L, int K, int Qi>
+constexpr int mrt_m = mrt::Table<L>::B.M[K][Qi];
+template <class L, int K>
+constexpr int mrt_group = mrt::Table<L>::B.group[K];
+
+template <class L, class T, int K, int Qi>
+__device__ __forceinline__ T mrt_acc(T acc, T g) {
+  constexpr int c = mrt_m<L, K, Qi>;
+  if constexpr (c == 0) return acc;
+  else if constexpr (c == 1) return acc + g;
+  else if constexpr (c == -1) return acc - g;
+  else return fma(T(c), g, acc);
+}
+
+template <class L, class T, int K, int... Qs>
+__device__ __forceinline__ T mrt_row(const T (&g)[L::Q], std::integer_sequence<int, Qs...>) {
+  T acc = T(0);
+  ((acc = mrt_acc<L, T, K, Qs>(acc, g[Qs])), ...);
+  return acc;
+}
+
+template <class L, class T, int K, int Qi>
+__device__ __forceinline__ T mrt_acc_nc(T acc, T d) {
+  if constexpr (mrt_group<L, K> < 0) return acc;  // conserved: delta is zero
+  else return mrt_acc<L, T, K, Qi>(acc, d);
+}
+
+template <class L, class T, int Qi, int... Ks>
+__device__ __forceinline__ T mrt_col(const T (&d)[L::Q], std::integer_sequence<int, Ks...>) {
+  T acc = T(0);
+  ((acc = mrt_acc_nc<L, T, Ks, Qi>(acc, d[Ks])), ...);
+  return acc;
+}
+
+template <class L, class T, int K>
+__device__ __forceinline__ T mrt_delta(const T (&g)[L::Q], const CollideParams& p) {
+  // conserved moments (group -1) have rate 0
+  if constexpr (mrt_group<L, K> < 0) return T(0);
+  else return mrt_factor<T>(p, K) * mrt_row<L, T, K>(g, std::make_integer_sequence<int, L::Q>{});
+}
+
+template <class L, class T, int... Ks>
+__device__ __forceinline__ void mrt_forward(const T (&g)[L::Q], T (&d)[L::Q], const CollideParams& p,
+                                            std::integer_sequence<int, Ks...>) {
+  ((d[Ks] = mrt_delta<L, T, Ks>(g, p)), ...);
+}
+
+template <class L, class T, int... Qs>
+__device__ __forceinline__ void mrt_backward(T (&h)[L::Q], const T (&d)[L::Q], const T (&G)[L::Q],
+                                             std::integer_sequence<int, Qs...>) {
+  ((h[Qs] = h[Qs] + G[Qs] - T(L::w(Qs)) * mrt_col<L, T, Qs>(d, std::make_integer_sequence<int, L::Q>{})), ...);
+}
+
+template <class L, class T>
+__device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p) {
+  const Macro<L, T> m = macro_from_h<L, T>(h, p);
+  const T usq15 = T(1.5) * (m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2]);
+  const T uF3 = T(3) * (m.u[0] * m.F[0] + m.u[1] * m.F[1] + m.u[2] * m.F[2]);
+  T g[L::Q], G[L::Q];
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    T ev, od;
+    heq_parts<L, T>(q, m, usq15, ev, od);
+    g[q] = h[q] - (ev + od);  // h^eq_q = even + odd part for direction q
+    G[q] = T(0);
+    if (p.has_force) {
+      T se, so;
+      guo_parts<L, T>(q, m, uF3, se, so);
+      G[q] = se + so;
+      g[q] += T(0.5) * G[q];
+    }
+  }
+  T d[L::Q];
+  mrt_forward<L, T>(g, d, p, std::make_integer_sequence<int, L::Q>{});
+  mrt_backward<L, T>(h, d, G, std::make_integer_sequence<int, L::Q>{});
+}
+
+}  // namespace lbm

@@ -1,0 +1,679 @@
+// Stream-collide sweep kernels and their helpers.
+//
+// Update patterns (Sec. IV-B "Streaming and Collision"):
+//   K_PULL     two arrays; cell x reads P_q(x - c_q) from src (pull), collides
+//              and writes dst[q][x].
+//   K_AA_EVEN  single array A; reads A[q][x], collides, writes the result of
+//              direction q to A[qbar][x] (in place, inverted).
+//   K_AA_ODD   reads A[qbar][x - c_q], collides, writes direction q to
+//              A[q][x + c_q].  Each thread touches only its own slots, so the
+//              update is race free.
+// Boundaries are compiled into the sweep (Sec. IV-B "Boundary Conditions"):
+// a per-cell link mask (bit q = the source x - c_q is not fluid) selects the
+// boundary value B_q(P(x)) of the cell's own post-collision populations:
+//   no-slip B_q = P_qbar; velocity bounce-back (UBB listing, Sec. III-C)
+//   B_q = P_qbar + 2 w_q (c_q.u_w)/c_s^2; outlet B_q = f^eq_q(rho_out, u_P).
+// In the AA pattern the producer of P(x) writes B_q into A[q][x] (the slot
+// the missing source cell would have filled), so even and odd steps read
+// boundary links like any other population.
+//
+// Memory layout: structure of arrays [q][N], N = nx*ny*nz, x fastest.  One
+// thread per cell, consecutive threads along x, so every population stream
+// is read and written by whole warps over consecutive addresses; the +-1
+// x-shift of a pull only offsets a warp's window by one element.
+#pragma once
+#include "lbm_collide.cuh"
+#include "lbm_cumulant.cuh"
+
+namespace lbm {
+
+enum Kind : int { K_PULL = 0, K_AA_EVEN = 1, K_AA_ODD = 2 };
+enum View : int { V_PULL = 0, V_AA_NATURAL = 1, V_AA_INVERTED = 2 };
+
+struct Geom {
+  int nx, ny, nz;
+  int per[3];
+  long long N;
+};
+
+struct SweepArgs {
+  const void* src;       // K_PULL: read array; AA: the single array
+  void* dst;             // K_PULL: write array; AA: the single array
+  const uint32_t* mask;  // link mask [N] or null
+  const uint8_t* flags;  // flag field [N] or null
+  Geom g;
+  CollideParams cp;
+  // start of each direction's stream in src / dst (src + q*N elements), so
+  // that every population access is one 32-bit cell offset from a base that
+  // lives in the kernel's constant bank
+  const char* srcq[27];
+  char* dstq[27];
+};
+
+constexpr int kBlockX = 128;
+
+// cell offsets of the 3x3x3 neighbourhood, periodic wrap (non-periodic
+// out-of-range neighbours are never dereferenced: their links are masked)
+struct Nbr {
+  int xo[3], yo[3], zo[3];
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const { return xo[dx + 1] + yo[dy + 1] + zo[dz + 1]; }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Geom& g, int x, int y, int z) {
+  Nbr n;
+  n.xo[0] = x == 0 ? g.nx - 1 : x - 1;
+  n.xo[1] = x;
+  n.xo[2] = x == g.nx - 1 ? 0 : x + 1;
+  const int sy = g.nx;
+  n.yo[0] = (y == 0 ? g.ny - 1 : y - 1) * sy;
+  n.yo[1] = y * sy;
+  n.yo[2] = (y == g.ny - 1 ? 0 : y + 1) * sy;
+  const int sz = g.nx * g.ny;
+  n.zo[0] = (z == 0 ? g.nz - 1 : z - 1) * sz;
+  n.zo[1] = z * sz;
+  n.zo[2] = (z == g.nz - 1 ? 0 : z + 1) * sz;
+  return n;
+}
+
+// Boundary type of the link whose source cell is (sx, sy, sz) (may lie one
+// cell outside the box).  Arguments are passed by value so that the rare
+// call never takes the address of the kernel's parameter block.
+static __device__ __noinline__ int link_type(const uint8_t* flags, int nx, int ny, int nz, int per_bits, int sx, int sy,
+                                      int sz) {
+  if (sx < 0 || sx >= nx) { if (!(per_bits & 1)) return L_NOSLIP; sx = (sx + nx) % nx; }
+  if (sy < 0 || sy >= ny) { if (!(per_bits & 2)) return L_NOSLIP; sy = (sy + ny) % ny; }
+  if (sz < 0 || sz >= nz) { if (!(per_bits & 4)) return L_NOSLIP; sz = (sz + nz) % nz; }
+  if (flags == nullptr) return L_NOSLIP;
+  return link_type_of_flag(flags[sx + nx * (sy + ny * sz)]);
+}
+
+__device__ __forceinline__ int per_bits(const Geom& g) {
+  return (g.per[0] ? 1 : 0) | (g.per[1] ? 2 : 0) | (g.per[2] ? 4 : 0);
+}
+
+#define LBM_LINK_TYPE(a, sx, sy, sz) \
+  link_type((a).flags, (a).g.nx, (a).g.ny, (a).g.nz, per_bits((a).g), (sx), (sy), (sz))
+
+// Parameters of the outlet condition, copied out of the kernel arguments.
+struct OutletP {
+  double F[3];
+  double rho_out;
+  int has_force;
+  int incompressible;
+};
+
+__device__ __forceinline__ OutletP outlet_params(const CollideParams& p) {
+  OutletP o;
+  o.F[0] = p.F[0]; o.F[1] = p.F[1]; o.F[2] = p.F[2];
+  o.rho_out = p.rho_out;
+  o.has_force = p.has_force;
+  o.incompressible = p.incompressible;
+  return o;
+}
+
+template <class L, class T>
+__device__ __forceinline__ T ubb_term(int q, const CollideParams& p) {
+  // 2 w_q (c_q . u_w) / c_s^2
+  const double cu = L::cx(q) * p.u_wall[0] + L::cy(q) * p.u_wall[1] + L::cz(q) * p.u_wall[2];
+  return T(6.0 * L::w(q) * cu);
+}
+
+// Value domain of populations in registers: DH = true holds h = f - w (shifted
+// storage, MRT, cumulant), DH = false holds f itself (unshifted storage with
+// SRT/TRT, which then needs no conversion at all).
+template <class ST, bool DH>
+struct Dom {
+  using T = typename ST::T;
+  using S = typename ST::S;
+  __device__ static __forceinline__ T load(S s, double w) {
+    if constexpr (DH) return ST::to_h(s, w);
+    else return T(s);
+  }
+  __device__ static __forceinline__ S store(T v, double w) {
+    if constexpr (DH) return ST::from_h(v, w);
+    else return S(v);
+  }
+};
+
+template <class ST, int OP>
+constexpr bool dom_h() {
+  return ST::shifted || !(OP == OP_SRT || OP == OP_TRT);
+}
+
+// Outlet value f^eq_q(rho_out, u) in the register domain (minus w_q if DH).
+template <class L, class T, bool DH>
+__device__ __forceinline__ T outlet_value(int q, const T (&u)[3], const OutletP& p) {
+  const T rho = T(p.rho_out);
+  const T rho0 = p.incompressible ? T(1) : rho;
+  const T cu = T(L::cx(q)) * u[0] + T(L::cy(q)) * u[1] + T(L::cz(q)) * u[2];
+  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T feq_dev = T(L::w(q)) * ((rho - T(1)) + rho0 * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+  return DH ? feq_dev : feq_dev + T(L::w(q));
+}
+
+// Velocity of post-collision populations: (sum c P - F/2) / rho_0(P).
+template <class L, class T, bool DH>
+__device__ __forceinline__ void post_velocity(const T (&v)[L::Q], const OutletP& p, T (&u)[3]) {
+  T r = T(0), j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    r += v[q];
+    j[0] += T(L::cx(q)) * v[q];
+    j[1] += T(L::cy(q)) * v[q];
+    j[2] += T(L::cz(q)) * v[q];
+  }
+  if (p.has_force) {
+    j[0] -= T(0.5 * p.F[0]); j[1] -= T(0.5 * p.F[1]); j[2] -= T(0.5 * p.F[2]);
+  }
+  const T rho = DH ? T(1) + r : r;
+  const T inv = T(1) / (p.incompressible ? T(1) : rho);
+  u[0] = j[0] * inv; u[1] = j[1] * inv; u[2] = L::D == 3 ? j[2] * inv : T(0);
+}
+
+// Value of an inlet or outlet pull link (x, q) whose no-slip value v_noslip
+// = P_qbar(x) has already been loaded.  Rare path (cells next to an inlet or
+// outlet), so it is not inlined and takes scalars only.
+template <class L, class ST, bool DH>
+__device__ __noinline__ typename ST::T pull_special(const typename ST::S* src, long long N, int cell, int q, int type,
+                                                    typename ST::T v_noslip, const OutletP p, double ubb) {
+  using T = typename ST::T;
+  if (type == L_INLET) return v_noslip + T(ubb);
+  if (type != L_OUTLET) return v_noslip;
+  T v[L::Q];
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) v[k] = Dom<ST, DH>::load(src[k * N + cell], L::w(k));
+  T u[3];
+  post_velocity<L, T, DH>(v, p, u);
+  return outlet_value<L, T, DH>(q, u, p);
+}
+
+template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_SRT>) {
+  collide_pairs<L, T, OP_SRT, DH>(v, p);
+}
+template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_TRT>) {
+  collide_pairs<L, T, OP_TRT, DH>(v, p);
+}
+template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_MRT>) {
+  static_assert(DH, "MRT works on shifted populations");
+  collide_mrt<L, T>(v, p);
+}
+template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_CUM>) {
+  static_assert(DH, "the cumulant operator works on shifted populations");
+  if constexpr (L::Q == 27) collide_cumulant<T>(v, p);
+}
+
+// ------------------------------------------------------------------- sweep
+// Boundary links are handled without branching on the common path: a
+// boundary link only changes which slot is read (pull, AA odd) or written (AA
+// odd), so the address is selected.  Inlet and outlet links, which also change
+// the value, exist only in cells flagged MASK_SPECIAL and are fixed up in a
+// rare divergent branch.
+template <class L, class ST, int OP, int KIND, bool BND>
+__global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
+  using T = typename ST::T;
+  using S = typename ST::S;
+  constexpr bool DH = dom_h<ST, OP>();
+  using D = Dom<ST, DH>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int cell = x + a.g.nx * (y + a.g.ny * z);
+  uint32_t mask = 0;
+  if constexpr (BND) {
+    mask = a.mask[cell];
+    if (mask & MASK_SOLID) return;
+  }
+  const Nbr nb = make_nbr(a.g, x, y, z);
+  T v[L::Q];
+
+  if constexpr (KIND == K_AA_EVEN) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) v[q] = D::load(reinterpret_cast<const S*>(a.srcq[q])[cell], L::w(q));
+  } else {
+    // pull:   fluid source -> P_q(x - c_q) = src[q][x - c_q];  boundary -> P_qbar(x) = src[qbar][x]
+    // AA odd: fluid source -> A[qbar][x - c_q];                 boundary -> A[q][x]
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      const bool b = BND && ((mask >> q) & 1u);
+      const int qs = (KIND == K_PULL) ? (b ? opp(q) : q) : (b ? q : opp(q));
+      const int idx = b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+      v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
+    }
+    if constexpr (KIND == K_PULL && BND) {
+      if (mask & MASK_SPECIAL) {
+        const OutletP op = outlet_params(a.cp);
+        for (int q = 1; q < L::Q; ++q) {
+          if ((mask >> q) & 1u) {
+            const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+            const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
+                                                L::cz(q) * a.cp.u_wall[2]);
+            v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb);
+          }
+        }
+      }
+    }
+  }
+
+  collide<L, T, DH>(v, a.cp, std::integral_constant<int, OP>{});
+
+  if constexpr (KIND == K_PULL) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = D::store(v[q], L::w(q));
+  } else {
+    if constexpr (BND) {
+      // inlet/outlet links (x, p = qbar): the slot A[p][x] receives B_p(P(x))
+      // instead of P_q(x); no-slip links keep P_q(x) = B_p(P(x)) unchanged
+      if (mask & MASK_SPECIAL) {
+        const OutletP op = outlet_params(a.cp);
+        T up[3];
+        post_velocity<L, T, DH>(v, op, up);
+#pragma unroll
+        for (int q = 1; q < L::Q; ++q) {
+          const int p = opp(q);
+          if ((mask >> p) & 1u) {
+            const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+            if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
+            else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      const int p = opp(q);
+      if constexpr (KIND == K_AA_EVEN) {
+        reinterpret_cast<S*>(a.dstq[p])[cell] = D::store(v[q], L::w(q));
+      } else {
+        // AA odd: fluid destination -> A[q][x + c_q]; boundary -> A[p][x]
+        const bool b = BND && ((mask >> p) & 1u);
+        const int qd = b ? p : q;
+        const int idx = b ? cell : nb.at(L::cx(q), L::cy(q), L::cz(q));
+        reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- gather (FP64)
+// Populations f(x) of the current time in FP64 (unshifted).
+template <class L, class ST>
+__device__ void gather_f64(const SweepArgs& a, int view, int x, int y, int z, int cell, uint32_t mask,
+                           double (&f)[L::Q]) {
+  using S = typename ST::S;
+  const S* A = static_cast<const S*>(a.src);
+  const long long N = a.g.N;
+  const Nbr nb = make_nbr(a.g, x, y, z);
+  if (view == V_AA_NATURAL) {
+    for (int q = 0; q < L::Q; ++q) f[q] = ST::to_f64(A[q * N + cell], L::w(q));
+    return;
+  }
+  if (view == V_AA_INVERTED) {
+    for (int q = 0; q < L::Q; ++q) {
+      if ((mask >> q) & 1u)
+        f[q] = ST::to_f64(A[q * N + cell], L::w(q));
+      else
+        f[q] = ST::to_f64(A[opp(q) * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q))], L::w(q));
+    }
+    return;
+  }
+  // pull: A holds P
+  double uP[3] = {0, 0, 0};
+  bool have_up = false;
+  for (int q = 0; q < L::Q; ++q) {
+    if ((mask >> q) & 1u) {
+      const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+      if (t == L_OUTLET) {
+        if (!have_up) {
+          double rho = 0, j[3] = {0, 0, 0};
+          for (int k = 0; k < L::Q; ++k) {
+            const double v = ST::to_f64(A[k * N + cell], L::w(k));
+            rho += v;
+            j[0] += L::cx(k) * v; j[1] += L::cy(k) * v; j[2] += L::cz(k) * v;
+          }
+          if (a.cp.has_force) for (int d = 0; d < 3; ++d) j[d] -= 0.5 * a.cp.F[d];
+          const double r0 = a.cp.incompressible ? 1.0 : rho;
+          for (int d = 0; d < 3; ++d) uP[d] = j[d] / r0;
+          if (L::D == 2) uP[2] = 0.0;
+          have_up = true;
+        }
+        const double rho = a.cp.rho_out;
+        const double rho0 = a.cp.incompressible ? 1.0 : rho;
+        const double cu = L::cx(q) * uP[0] + L::cy(q) * uP[1] + L::cz(q) * uP[2];
+        const double usq = uP[0] * uP[0] + uP[1] * uP[1] + uP[2] * uP[2];
+        f[q] = L::w(q) * (rho + rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+      } else {
+        double v = ST::to_f64(A[opp(q) * N + cell], L::w(q));
+        if (t == L_INLET)
+          v += 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] + L::cz(q) * a.cp.u_wall[2]);
+        f[q] = v;
+      }
+    } else {
+      f[q] = ST::to_f64(A[q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q))], L::w(q));
+    }
+  }
+}
+
+template <class L>
+__device__ __forceinline__ void moments_f64(const double (&f)[L::Q], const CollideParams& p, double& rho,
+                                            double& rho0, double (&u)[3]) {
+  double j[3] = {0, 0, 0};
+  rho = 0;
+  for (int q = 0; q < L::Q; ++q) {
+    rho += f[q];
+    j[0] += L::cx(q) * f[q];
+    j[1] += L::cy(q) * f[q];
+    j[2] += L::cz(q) * f[q];
+  }
+  if (p.has_force) for (int d = 0; d < 3; ++d) j[d] += 0.5 * p.F[d];
+  rho0 = p.incompressible ? 1.0 : rho;
+  for (int d = 0; d < 3; ++d) u[d] = j[d] / rho0;
+  if (L::D == 2) u[2] = 0.0;
+}
+
+__device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& x, int& y, int& z) {
+  x = (int)(cell % g.nx);
+  const long long r = cell / g.nx;
+  y = (int)(r % g.ny);
+  z = (int)(r / g.ny);
+}
+
+template <class L, class ST>
+__global__ void k_populations(const SweepArgs a, int view, double* __restrict__ out) {
+  const long long N = a.g.N;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const uint32_t mask = a.mask ? a.mask[cell] : 0u;
+    if (mask & MASK_SOLID) {
+      for (int q = 0; q < L::Q; ++q) out[q * N + cell] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    double f[L::Q];
+    gather_f64<L, ST>(a, view, x, y, z, (int)cell, mask, f);
+    for (int q = 0; q < L::Q; ++q) out[q * N + cell] = f[q];
+  }
+}
+
+template <class L, class ST, class OUT>
+__global__ void k_macroscopic(const SweepArgs a, int view, OUT* __restrict__ rho_out, OUT* __restrict__ u_out) {
+  const long long N = a.g.N;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const uint32_t mask = a.mask ? a.mask[cell] : 0u;
+    if (mask & MASK_SOLID) {
+      const OUT nan = OUT(__longlong_as_double(0x7ff8000000000000LL));
+      rho_out[cell] = nan;
+      for (int d = 0; d < L::D; ++d) u_out[d * N + cell] = nan;
+      continue;
+    }
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    double f[L::Q];
+    gather_f64<L, ST>(a, view, x, y, z, (int)cell, mask, f);
+    double rho, rho0, u[3];
+    moments_f64<L>(f, a.cp, rho, rho0, u);
+    rho_out[cell] = OUT(rho);
+    for (int d = 0; d < L::D; ++d) u_out[d * N + cell] = OUT(u[d]);
+  }
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP64 partial sums (mass, momentum[3], kinetic energy) per block; the
+// partials array is caller-provided scratch of gridDim.x * 5 doubles.
+template <class L, class ST>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const SweepArgs a, int view, double* partials) {
+  const long long N = a.g.N;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const uint32_t mask = a.mask ? a.mask[cell] : 0u;
+    if (mask & MASK_SOLID) continue;
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    double f[L::Q];
+    gather_f64<L, ST>(a, view, x, y, z, (int)cell, mask, f);
+    double rho, rho0, u[3];
+    moments_f64<L>(f, a.cp, rho, rho0, u);
+    acc[0] += rho;
+    acc[1] += rho0 * u[0];
+    acc[2] += rho0 * u[1];
+    acc[3] += rho0 * u[2];
+    acc[4] += 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  }
+  __shared__ double sh[kRedThreads / 32][5];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = 0; i < 5; ++i) {
+    const double v = warp_sum(acc[i]);
+    if (lane == 0) sh[wid][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sh[w][threadIdx.x];
+    partials[blockIdx.x * 5 + threadIdx.x] = s;
+  }
+}
+
+// Sum nblocks partial rows into out[5] (one block, fixed order).
+__global__ void k_reduce_final(const double* partials, int nblocks, double* out);
+
+template <class L>
+__global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask) {
+  const long long N = a.g.N;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    if (a.flags != nullptr && a.flags[cell] != 0) {
+      mask[cell] = MASK_SOLID;
+      continue;
+    }
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    uint32_t m = 0;
+    for (int q = 1; q < L::Q; ++q) {
+      int sx = x - L::cx(q), sy = y - L::cy(q), sz = z - L::cz(q);
+      bool solid = false;
+      if (sx < 0 || sx >= a.g.nx) { if (!a.g.per[0]) solid = true; else sx = (sx + a.g.nx) % a.g.nx; }
+      if (sy < 0 || sy >= a.g.ny) { if (!a.g.per[1]) solid = true; else sy = (sy + a.g.ny) % a.g.ny; }
+      if (sz < 0 || sz >= a.g.nz) { if (!a.g.per[2]) solid = true; else sz = (sz + a.g.nz) % a.g.nz; }
+      int type = L_NOSLIP;
+      if (!solid && a.flags != nullptr) {
+        const uint8_t f = a.flags[sx + a.g.nx * (sy + a.g.ny * sz)];
+        solid = f != 0;
+        if (solid) type = link_type_of_flag(f);
+      }
+      if (solid) {
+        m |= 1u << q;
+        if (type != L_NOSLIP) m |= MASK_SPECIAL;
+      }
+    }
+    mask[cell] = m;
+  }
+}
+
+// Initialisation / state upload.  src_kind 0: P from an FP64 array P[q][N];
+// src_kind 1: P = f^eq(rho[N], u[d][N]) (Eq. discrete_eq).  pattern K_PULL
+// writes P; pattern AA writes the natural (even-parity) layout, i.e. the
+// streamed populations f_q(x) = P_q(x - c_q), or B_q(P(x)) on boundary links.
+template <class L>
+__device__ __forceinline__ double state_value(const double* P, const double* rho, const double* u, int src_kind,
+                                              long long N, int q, long long cell, const CollideParams& p) {
+  if (src_kind == 0) return P[q * N + cell];
+  const double r = rho[cell];
+  const double r0 = p.incompressible ? 1.0 : r;
+  double uu[3] = {u[cell], u[N + cell], L::D == 3 ? u[2 * N + cell] : 0.0};
+  const double cu = L::cx(q) * uu[0] + L::cy(q) * uu[1] + L::cz(q) * uu[2];
+  const double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+  return L::w(q) * (r + r0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+}
+
+template <class L, class ST>
+__global__ void k_set_state(const SweepArgs a, int aa, int src_kind, const double* P, const double* rho,
+                            const double* u) {
+  using S = typename ST::S;
+  S* A = static_cast<S*>(a.dst);
+  const long long N = a.g.N;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const uint32_t mask = a.mask ? a.mask[cell] : 0u;
+    if (!aa || (mask & MASK_SOLID)) {
+      for (int q = 0; q < L::Q; ++q)
+        A[q * N + cell] = ST::from_f64(state_value<L>(P, rho, u, src_kind, N, q, cell, a.cp), L::w(q));
+      continue;
+    }
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    const Nbr nb = make_nbr(a.g, x, y, z);
+    double uP[3] = {0, 0, 0};
+    bool have_up = false;
+    for (int q = 0; q < L::Q; ++q) {
+      double v;
+      if ((mask >> q) & 1u) {
+        const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+        if (t == L_OUTLET) {
+          if (!have_up) {
+            double r = 0, j[3] = {0, 0, 0};
+            for (int k = 0; k < L::Q; ++k) {
+              const double pv = state_value<L>(P, rho, u, src_kind, N, k, cell, a.cp);
+              r += pv;
+              j[0] += L::cx(k) * pv; j[1] += L::cy(k) * pv; j[2] += L::cz(k) * pv;
+            }
+            if (a.cp.has_force) for (int d = 0; d < 3; ++d) j[d] -= 0.5 * a.cp.F[d];
+            const double r0 = a.cp.incompressible ? 1.0 : r;
+            for (int d = 0; d < 3; ++d) uP[d] = j[d] / r0;
+            if (L::D == 2) uP[2] = 0.0;
+            have_up = true;
+          }
+          const double ro = a.cp.rho_out;
+          const double ro0 = a.cp.incompressible ? 1.0 : ro;
+          const double cu = L::cx(q) * uP[0] + L::cy(q) * uP[1] + L::cz(q) * uP[2];
+          const double usq = uP[0] * uP[0] + uP[1] * uP[1] + uP[2] * uP[2];
+          v = L::w(q) * (ro + ro0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+        } else {
+          v = state_value<L>(P, rho, u, src_kind, N, opp(q), cell, a.cp);
+          if (t == L_INLET)
+            v += 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] + L::cz(q) * a.cp.u_wall[2]);
+        }
+      } else {
+        const long long s = nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+        v = state_value<L>(P, rho, u, src_kind, N, q, s, a.cp);
+      }
+      A[q * N + cell] = ST::from_f64(v, L::w(q));
+    }
+  }
+}
+
+// --------------------------------------------------------------- launchers
+inline dim3 sweep_block(const Geom& g) {
+  int bx = g.nx >= kBlockX ? kBlockX : ((g.nx + 31) / 32) * 32;
+  return dim3(bx, 1, 1);
+}
+inline dim3 sweep_grid(const Geom& g) {
+  const dim3 b = sweep_block(g);
+  return dim3((g.nx + b.x - 1) / b.x, g.ny, g.nz);
+}
+
+template <class L, class ST, int OP, int KIND>
+cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
+  if (bnd)
+    k_sweep<L, ST, OP, KIND, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
+  else
+    k_sweep<L, ST, OP, KIND, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class L, class ST, int OP>
+cudaError_t launch_sweep_op(int kind, bool bnd, const SweepArgs& a, cudaStream_t s) {
+  switch (kind) {
+    case K_PULL: return launch_sweep_k<L, ST, OP, K_PULL>(bnd, a, s);
+    case K_AA_EVEN: return launch_sweep_k<L, ST, OP, K_AA_EVEN>(bnd, a, s);
+    case K_AA_ODD: return launch_sweep_k<L, ST, OP, K_AA_ODD>(bnd, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+inline int grid_stride_blocks(long long N, int threads) {
+  long long b = (N + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// Everything that depends on (stencil, storage): explicitly instantiated in
+// one translation unit per pair.
+template <class L, class ST>
+struct Ops {
+  static cudaError_t sweep(int op, int kind, bool bnd, const SweepArgs& a, cudaStream_t s) {
+    switch (op) {
+      case OP_SRT: return launch_sweep_op<L, ST, OP_SRT>(kind, bnd, a, s);
+      case OP_TRT: return launch_sweep_op<L, ST, OP_TRT>(kind, bnd, a, s);
+      case OP_MRT: return launch_sweep_op<L, ST, OP_MRT>(kind, bnd, a, s);
+      case OP_CUM:
+        if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s);
+        return cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t populations(int view, const SweepArgs& a, double* out, cudaStream_t s) {
+    k_populations<L, ST><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t macroscopic(int view, const SweepArgs& a, void* rho, void* u, bool f64, cudaStream_t s) {
+    if (f64)
+      k_macroscopic<L, ST, double><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, (double*)rho, (double*)u);
+    else
+      k_macroscopic<L, ST, float><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, (float*)rho, (float*)u);
+    return cudaGetLastError();
+  }
+  static cudaError_t reduce_partial(int view, const SweepArgs& a, double* partials, int nblocks, cudaStream_t s) {
+    k_reduce_partial<L, ST><<<nblocks, kRedThreads, 0, s>>>(a, view, partials);
+    return cudaGetLastError();
+  }
+  static cudaError_t set_state(bool aa, int src_kind, const SweepArgs& a, const double* P, const double* rho,
+                               const double* u, cudaStream_t s) {
+    k_set_state<L, ST><<<grid_stride_blocks(a.g.N, 128), 128, 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
+    return cudaGetLastError();
+  }
+};
+
+template <class L>
+cudaError_t launch_link_mask(const SweepArgs& a, uint32_t* mask, cudaStream_t s) {
+  k_link_mask<L><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, mask);
+  return cudaGetLastError();
+}
+
+// Dispatch table of one (stencil, storage) pair.  Each lbm_inst_*.cu defines
+// one factory returning it, so the C ABI unit instantiates no kernels.
+struct OpsTable {
+  cudaError_t (*sweep)(int, int, bool, const SweepArgs&, cudaStream_t);
+  cudaError_t (*populations)(int, const SweepArgs&, double*, cudaStream_t);
+  cudaError_t (*macroscopic)(int, const SweepArgs&, void*, void*, bool, cudaStream_t);
+  cudaError_t (*reduce_partial)(int, const SweepArgs&, double*, int, cudaStream_t);
+  cudaError_t (*set_state)(bool, int, const SweepArgs&, const double*, const double*, const double*, cudaStream_t);
+  cudaError_t (*link_mask)(const SweepArgs&, uint32_t*, cudaStream_t);
+};
+
+template <class L, class ST>
+OpsTable make_table() {
+  return OpsTable{&Ops<L, ST>::sweep,          &Ops<L, ST>::populations, &Ops<L, ST>::macroscopic,
+                  &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>};
+}
+
+#define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();
+#define LBM_ALL_TABLES(X) \
+  X(d2q9, f64) X(d2q9, f32) X(d2q9, f16s) X(d2q9, f32s) \
+  X(d3q19, f64) X(d3q19, f32) X(d3q19, f16s) X(d3q19, f32s) \
+  X(d3q27, f64) X(d3q27, f32) X(d3q27, f16s) X(d3q27, f32s)
+LBM_ALL_TABLES(LBM_TABLE_DECL)
+
+}  // namespace lbm

@@ -137,4 +137,6 @@ def test_link_mask_brute_force():
                 sx, sy, sz = (x - c[0]) % 6, y - c[1], (z - c[2]) % 4
                 if not (0 <= sy < 5) or flags[sz, sy, sx] != 0:
                     ref |= 1 << q
+                    if 0 <= sy < 5 and flags[sz, sy, sx] in (lbm.INLET, lbm.OUTLET):
+                        ref |= 1 << 30
         assert mask[z, y, x] == ref, (z, y, x)

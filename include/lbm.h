@@ -182,6 +182,30 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const void* src, int64_t t);
  * Computed on the device from the flags. */
 lbm_status lbm_link_mask(lbm_ctx* ctx, uint32_t* mask);
 
+/* The sums of lbm_reduce without a context and without any allocation, for
+ * callers that cannot allocate device memory: for example a host application
+ * whose GPU memory belongs to another allocator that reserves it at start-up,
+ * or a time-step loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation.  The paper has no counterpart; it exists for such callers.
+ *   p:      the parameters the populations were produced with (validated as in
+ *           lbm_query_sizes);
+ *   pdf:    device population array in the native layout, as lbm_get_pdfs
+ *           returns it (for LBM_PULL the array holding the current state);
+ *   flags:  device uint8[N] flag field or NULL (all fluid);
+ *   t:      the step count of that state (selects the AA parity);
+ *   out:    device double[5]; receives the same five sums as lbm_reduce;
+ *   stream: cudaStream_t (NULL = legacy default stream); the call enqueues work
+ *           and returns without synchronising.
+ * Scratch lives in a fixed 160 KiB array in the library's device memory that
+ * every GPU which loads the library keeps until the process exits.  The first
+ * call on each device (with that device current) looks up the array's device
+ * address, so make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU race.  Returns LBM_E_INVAL
+ * for more than 67,108,864 cells (the cells the fixed scratch covers), and
+ * never calls cudaMalloc or cudaFree. */
+lbm_status lbm_reduce_noalloc(const lbm_params* p, const void* pdf, const uint8_t* flags, int64_t t,
+                              double* out, void* stream);
+
 /* Block until the context's stream is idle; maps pending CUDA errors. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 

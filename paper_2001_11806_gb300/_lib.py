@@ -54,6 +54,7 @@ _SIGS = {
     "lbm_get_pdfs": (c_int32, [c_void_p, c_void_p]),
     "lbm_set_pdfs": (c_int32, [c_void_p, c_void_p, c_int64]),
     "lbm_link_mask": (c_int32, [c_void_p, c_void_p]),
+    "lbm_reduce_noalloc": (c_int32, [POINTER(Params), c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "lbm_sync": (c_int32, [c_void_p]),
     "lbm_status_str": (c_char_p, [c_int32]),
     "lbm_last_error": (c_char_p, [c_void_p]),

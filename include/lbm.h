@@ -182,6 +182,43 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const void* src, int64_t t);
  * Computed on the device from the flags. */
 lbm_status lbm_link_mask(lbm_ctx* ctx, uint32_t* mask);
 
+/* Replace the uniform body force (Guo scheme); takes effect for later
+ * launches. */
+lbm_status lbm_set_force(lbm_ctx* ctx, const double F[3]);
+
+/* One time step of the pull pattern from the population array src into dst
+ * (both pdf_bytes, distinct; the context's own arrays are not touched).
+ * LBM_E_STATE for an AA context.  Used to recompute checkpoint segments. */
+lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
+
+/* Discrete adjoint of one pull time step (the paper has no adjoint; this is
+ * the reverse-mode derivative of the sweep): lam_out = S^T C'(f)^T lam_in,
+ * with f = S(P_prev) the populations the forward step collided (S = pull
+ * streaming with boundary links, C = collision).  If dLdF is non-NULL, the
+ * body-force gradient of the step, sum_x (dC/dF)^T lam_in, is added to the
+ * device double[3] it points to.  lam_in, lam_out: device [q][N] arrays of FP64
+ * when storage is LBM_F64, else FP32 (distinct).  P_prev: device population
+ * array in the storage type.  Requires the pull pattern (LBM_E_STATE), SRT,
+ * TRT or MRT (LBM_E_UNSUPPORTED for cumulant) and no OUTLET links
+ * (LBM_E_UNSUPPORTED).  Non-fluid cells receive zero. */
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* P_prev, const void* lam_in, void* lam_out,
+                            double* dLdF);
+
+/* Kinetic energy in a box, L = (1/2) sum rho |u|^2 over the fluid cells with
+ * box[0] <= x < box[1], box[2] <= y < box[3], box[4] <= z < box[5], of the
+ * populations f = S(P) (u with the Guo half force), ADDED to the device
+ * double *L.  If lam_out is non-NULL it receives the adjoint seed
+ * S^T dL/df (layout and type as in lbm_adjoint_step); if dLdF is non-NULL the
+ * explicit body-force derivative of L is added to it.  Same requirements as
+ * lbm_adjoint_step. */
+lbm_status lbm_ke_loss_seed(lbm_ctx* ctx, const void* P, const int32_t box[6], double* L, void* lam_out,
+                            double* dLdF);
+
+/* g_u0 = (d f^eq(rho_0, u_0) / d u_0)^T lam for the initial state written by
+ * lbm_init_equilibrium: rho0[N], u0[d][N] and g_u0[d][N] are device FP64, lam
+ * as in lbm_adjoint_step.  Non-fluid cells receive zero. */
+lbm_status lbm_eq_vjp(lbm_ctx* ctx, const double* rho0, const double* u0, const void* lam, double* g_u0);
+
 /* The sums of lbm_reduce without a context and without any allocation, for
  * callers that cannot allocate device memory: for example a host application
  * whose GPU memory belongs to another allocator that reserves it at start-up,

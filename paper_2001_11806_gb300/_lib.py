@@ -54,6 +54,11 @@ _SIGS = {
     "lbm_get_pdfs": (c_int32, [c_void_p, c_void_p]),
     "lbm_set_pdfs": (c_int32, [c_void_p, c_void_p, c_int64]),
     "lbm_link_mask": (c_int32, [c_void_p, c_void_p]),
+    "lbm_set_force": (c_int32, [c_void_p, POINTER(c_double)]),
+    "lbm_step_pull": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "lbm_adjoint_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_ke_loss_seed": (c_int32, [c_void_p, c_void_p, POINTER(c_int32), c_void_p, c_void_p, c_void_p]),
+    "lbm_eq_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_reduce_noalloc": (c_int32, [POINTER(Params), c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "lbm_sync": (c_int32, [c_void_p]),
     "lbm_status_str": (c_char_p, [c_int32]),

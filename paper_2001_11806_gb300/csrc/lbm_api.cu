@@ -9,7 +9,7 @@
 #include <string>
 
 #include "../../include/lbm.h"
-#include "lbm_kernels.cuh"
+#include "lbm_ops.cuh"
 
 namespace lbm {
 __global__ void k_reduce_final(const double* partials, int nblocks, double* out) {
@@ -65,6 +65,7 @@ struct lbm_ctx {
   double* partials = nullptr;
   double* result = nullptr;
   bool has_mask = false;
+  unsigned link_types = 0;  // OR of the boundary-link types present (L_INLET, L_OUTLET)
   cudaStream_t stream = nullptr;
   int64_t t = 0;
   CollideParams cp;
@@ -290,7 +291,12 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
   c->ops = get_table(p->stencil, p->storage);
   if (mask) {
     SweepArgs a = make_args(c, nullptr, nullptr);
-    cudaError_t e = c->ops.link_mask(a, c->mask, c->stream);
+    unsigned* types = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(c->result) + 64);
+    cudaError_t e = cudaMemsetAsync(types, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = c->ops.link_mask(a, c->mask, types, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&c->link_types, types, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       delete c;
       return LBM_E_CUDA;
@@ -409,6 +415,73 @@ lbm_status lbm_link_mask(lbm_ctx* c, uint32_t* mask) {
     e = cudaMemsetAsync(mask, 0, size_t(c->N) * 4, c->stream);
   }
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "link_mask");
+}
+
+lbm_status lbm_set_force(lbm_ctx* c, const double F[3]) {
+  if (!c || !F) return LBM_E_INVAL;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(F[i])) return LBM_E_INVAL;
+  if (c->p.collision == LBM_CUMULANT && (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0)) return LBM_E_UNSUPPORTED;
+  for (int i = 0; i < 3; ++i) c->p.force[i] = F[i];
+  fill_collide_params(c);
+  return LBM_OK;
+}
+
+lbm_status lbm_step_pull(lbm_ctx* c, const void* src, void* dst) {
+  if (!c || !src || !dst || src == dst) return LBM_E_INVAL;
+  if (c->p.pattern != LBM_PULL) return LBM_E_STATE;
+  SweepArgs a = make_args(c, src, dst);
+  cudaError_t e = c->ops.sweep(c->p.collision, K_PULL, c->has_mask, a, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "step_pull");
+}
+
+namespace {
+lbm_status adjoint_ok(lbm_ctx* c) {
+  if (c->p.pattern != LBM_PULL) {
+    c->err = "the adjoint works on the two-array pull layout";
+    return LBM_E_STATE;
+  }
+  if (c->p.collision == LBM_CUMULANT) {
+    c->err = "the cumulant operator has no adjoint";
+    return LBM_E_UNSUPPORTED;
+  }
+  if (c->link_types & L_OUTLET) {
+    c->err = "outlet links are not differentiated";
+    return LBM_E_UNSUPPORTED;
+  }
+  return LBM_OK;
+}
+}  // namespace
+
+lbm_status lbm_adjoint_step(lbm_ctx* c, const void* P_prev, const void* lam_in, void* lam_out, double* dLdF) {
+  if (!c || !P_prev || !lam_in || !lam_out || lam_in == lam_out) return LBM_E_INVAL;
+  lbm_status st = adjoint_ok(c);
+  if (st != LBM_OK) return st;
+  SweepArgs a = make_args(c, P_prev, nullptr);
+  cudaError_t e = c->ops.adjoint(c->p.collision, c->has_mask, a, lam_in, lam_out, dLdF, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "adjoint_step");
+}
+
+lbm_status lbm_ke_loss_seed(lbm_ctx* c, const void* P, const int32_t box[6], double* L, void* lam_out,
+                            double* dLdF) {
+  if (!c || !P || !box || !L) return LBM_E_INVAL;
+  lbm_status st = adjoint_ok(c);
+  if (st != LBM_OK) return st;
+  const int32_t n[3] = {c->p.nx, c->p.ny, c->p.nz};
+  for (int a = 0; a < 3; ++a)
+    if (box[2 * a] < 0 || box[2 * a + 1] > n[a] || box[2 * a] > box[2 * a + 1]) return LBM_E_INVAL;
+  SweepArgs a = make_args(c, P, nullptr);
+  int b[6];
+  for (int i = 0; i < 6; ++i) b[i] = box[i];
+  cudaError_t e = c->ops.ke_seed(c->has_mask, a, b, L, lam_out, dLdF, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "ke_loss_seed");
+}
+
+lbm_status lbm_eq_vjp(lbm_ctx* c, const double* rho0, const double* u0, const void* lam, double* g_u0) {
+  if (!c || !rho0 || !u0 || !lam || !g_u0) return LBM_E_INVAL;
+  SweepArgs a = make_args(c, nullptr, nullptr);
+  cudaError_t e = c->ops.eq_vjp(a, rho0, u0, lam, g_u0, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "eq_vjp");
 }
 
 lbm_status lbm_sync(lbm_ctx* c) {

@@ -243,6 +243,13 @@ __device__ __forceinline__ void mrt_backward(T (&h)[L::Q], const T (&d)[L::Q], c
   ((h[Qs] = h[Qs] + G[Qs] - T(L::w(Qs)) * mrt_col<L, T, Qs>(d, std::make_integer_sequence<int, L::Q>{})), ...);
 }
 
+// nu_q = sum_k M_kq d_k over the non-conserved moments (M^T d, no weights)
+template <class L, class T, int... Qs>
+__device__ __forceinline__ void mrt_transpose_back(const T (&d)[L::Q], T (&nu)[L::Q],
+                                                   std::integer_sequence<int, Qs...>) {
+  ((nu[Qs] = mrt_col<L, T, Qs>(d, std::make_integer_sequence<int, L::Q>{})), ...);
+}
+
 template <class L, class T>
 __device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p) {
   const Macro<L, T> m = macro_from_h<L, T>(h, p);

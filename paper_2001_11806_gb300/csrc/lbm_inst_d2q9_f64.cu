@@ -1,6 +1,6 @@
 // Explicit instantiation of every kernel for the D2Q9 stencil with F64 storage
 // (one translation unit per pair so that the build compiles them in parallel).
-#include "lbm_kernels.cuh"
+#include "lbm_ops.cuh"
 
 namespace lbm {
 OpsTable ops_table_d2q9_f64() { return make_table<D2Q9, StF64>(); }

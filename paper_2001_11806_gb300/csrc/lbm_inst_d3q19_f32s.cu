@@ -1,6 +1,6 @@
 // Explicit instantiation of every kernel for the D3Q19 stencil with F32S storage
 // (one translation unit per pair so that the build compiles them in parallel).
-#include "lbm_kernels.cuh"
+#include "lbm_ops.cuh"
 
 namespace lbm {
 OpsTable ops_table_d3q19_f32s() { return make_table<D3Q19, StF32S>(); }

@@ -469,8 +469,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const SweepArgs 
 // Sum nblocks partial rows into out[5] (one block, fixed order).
 __global__ void k_reduce_final(const double* partials, int nblocks, double* out);
 
+// Also ORs the types of all boundary links into *types (may be null).
 template <class L>
-__global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask) {
+__global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsigned* types) {
   const long long N = a.g.N;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
        cell += (long long)gridDim.x * blockDim.x) {
@@ -496,6 +497,7 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask) {
       if (solid) {
         m |= 1u << q;
         if (type != L_NOSLIP) m |= MASK_SPECIAL;
+        if (types != nullptr && type != L_NOSLIP) atomicOr(types, unsigned(type));
       }
     }
     mask[cell] = m;
@@ -608,72 +610,5 @@ inline int grid_stride_blocks(long long N, int threads) {
   if (b > 152 * 16) b = 152 * 16;
   return (int)(b < 1 ? 1 : b);
 }
-
-// Everything that depends on (stencil, storage): explicitly instantiated in
-// one translation unit per pair.
-template <class L, class ST>
-struct Ops {
-  static cudaError_t sweep(int op, int kind, bool bnd, const SweepArgs& a, cudaStream_t s) {
-    switch (op) {
-      case OP_SRT: return launch_sweep_op<L, ST, OP_SRT>(kind, bnd, a, s);
-      case OP_TRT: return launch_sweep_op<L, ST, OP_TRT>(kind, bnd, a, s);
-      case OP_MRT: return launch_sweep_op<L, ST, OP_MRT>(kind, bnd, a, s);
-      case OP_CUM:
-        if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s);
-        return cudaErrorInvalidValue;
-    }
-    return cudaErrorInvalidValue;
-  }
-  static cudaError_t populations(int view, const SweepArgs& a, double* out, cudaStream_t s) {
-    k_populations<L, ST><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, out);
-    return cudaGetLastError();
-  }
-  static cudaError_t macroscopic(int view, const SweepArgs& a, void* rho, void* u, bool f64, cudaStream_t s) {
-    if (f64)
-      k_macroscopic<L, ST, double><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, (double*)rho, (double*)u);
-    else
-      k_macroscopic<L, ST, float><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, (float*)rho, (float*)u);
-    return cudaGetLastError();
-  }
-  static cudaError_t reduce_partial(int view, const SweepArgs& a, double* partials, int nblocks, cudaStream_t s) {
-    k_reduce_partial<L, ST><<<nblocks, kRedThreads, 0, s>>>(a, view, partials);
-    return cudaGetLastError();
-  }
-  static cudaError_t set_state(bool aa, int src_kind, const SweepArgs& a, const double* P, const double* rho,
-                               const double* u, cudaStream_t s) {
-    k_set_state<L, ST><<<grid_stride_blocks(a.g.N, 128), 128, 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
-    return cudaGetLastError();
-  }
-};
-
-template <class L>
-cudaError_t launch_link_mask(const SweepArgs& a, uint32_t* mask, cudaStream_t s) {
-  k_link_mask<L><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, mask);
-  return cudaGetLastError();
-}
-
-// Dispatch table of one (stencil, storage) pair.  Each lbm_inst_*.cu defines
-// one factory returning it, so the C ABI unit instantiates no kernels.
-struct OpsTable {
-  cudaError_t (*sweep)(int, int, bool, const SweepArgs&, cudaStream_t);
-  cudaError_t (*populations)(int, const SweepArgs&, double*, cudaStream_t);
-  cudaError_t (*macroscopic)(int, const SweepArgs&, void*, void*, bool, cudaStream_t);
-  cudaError_t (*reduce_partial)(int, const SweepArgs&, double*, int, cudaStream_t);
-  cudaError_t (*set_state)(bool, int, const SweepArgs&, const double*, const double*, const double*, cudaStream_t);
-  cudaError_t (*link_mask)(const SweepArgs&, uint32_t*, cudaStream_t);
-};
-
-template <class L, class ST>
-OpsTable make_table() {
-  return OpsTable{&Ops<L, ST>::sweep,          &Ops<L, ST>::populations, &Ops<L, ST>::macroscopic,
-                  &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>};
-}
-
-#define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();
-#define LBM_ALL_TABLES(X) \
-  X(d2q9, f64) X(d2q9, f32) X(d2q9, f16s) X(d2q9, f32s) \
-  X(d3q19, f64) X(d3q19, f32) X(d3q19, f16s) X(d3q19, f32s) \
-  X(d3q27, f64) X(d3q27, f32) X(d3q27, f16s) X(d3q27, f32s)
-LBM_ALL_TABLES(LBM_TABLE_DECL)
 
 }  // namespace lbm

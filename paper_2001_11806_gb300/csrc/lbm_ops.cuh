@@ -1,0 +1,113 @@
+// Dispatch tables: everything that depends on (stencil, storage) is
+// reached through one OpsTable per pair, built in lbm_inst_*.cu.
+#pragma once
+#include "lbm_adjoint.cuh"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// Everything that depends on (stencil, storage): explicitly instantiated in
+// one translation unit per pair.
+template <class L, class ST>
+struct Ops {
+  static cudaError_t sweep(int op, int kind, bool bnd, const SweepArgs& a, cudaStream_t s) {
+    switch (op) {
+      case OP_SRT: return launch_sweep_op<L, ST, OP_SRT>(kind, bnd, a, s);
+      case OP_TRT: return launch_sweep_op<L, ST, OP_TRT>(kind, bnd, a, s);
+      case OP_MRT: return launch_sweep_op<L, ST, OP_MRT>(kind, bnd, a, s);
+      case OP_CUM:
+        if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s);
+        return cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t populations(int view, const SweepArgs& a, double* out, cudaStream_t s) {
+    k_populations<L, ST><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t macroscopic(int view, const SweepArgs& a, void* rho, void* u, bool f64, cudaStream_t s) {
+    if (f64)
+      k_macroscopic<L, ST, double><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, (double*)rho, (double*)u);
+    else
+      k_macroscopic<L, ST, float><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, view, (float*)rho, (float*)u);
+    return cudaGetLastError();
+  }
+  static cudaError_t reduce_partial(int view, const SweepArgs& a, double* partials, int nblocks, cudaStream_t s) {
+    k_reduce_partial<L, ST><<<nblocks, kRedThreads, 0, s>>>(a, view, partials);
+    return cudaGetLastError();
+  }
+  static cudaError_t set_state(bool aa, int src_kind, const SweepArgs& a, const double* P, const double* rho,
+                               const double* u, cudaStream_t s) {
+    k_set_state<L, ST><<<grid_stride_blocks(a.g.N, 128), 128, 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
+    return cudaGetLastError();
+  }
+  using T = typename ST::T;
+  template <int OP>
+  static cudaError_t adjoint_op(bool bnd, const SweepArgs& a, const void* li, void* lo, double* dF, cudaStream_t s) {
+    if (bnd)
+      k_adjoint<L, ST, OP, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, (const T*)li, (T*)lo, dF);
+    else
+      k_adjoint<L, ST, OP, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, (const T*)li, (T*)lo, dF);
+    return cudaGetLastError();
+  }
+  static cudaError_t adjoint(int op, bool bnd, const SweepArgs& a, const void* li, void* lo, double* dF,
+                             cudaStream_t s) {
+    switch (op) {
+      case OP_SRT: return adjoint_op<OP_SRT>(bnd, a, li, lo, dF, s);
+      case OP_TRT: return adjoint_op<OP_TRT>(bnd, a, li, lo, dF, s);
+      case OP_MRT: return adjoint_op<OP_MRT>(bnd, a, li, lo, dF, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t ke_seed(bool bnd, const SweepArgs& a, const int* box, double* loss, void* lo, double* dF,
+                             cudaStream_t s) {
+    const int4 lo4 = make_int4(box[0], box[2], box[4], 0), hi4 = make_int4(box[1], box[3], box[5], 0);
+    if (bnd)
+      k_ke_seed<L, ST, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, lo4, hi4, loss, (T*)lo, dF);
+    else
+      k_ke_seed<L, ST, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, lo4, hi4, loss, (T*)lo, dF);
+    return cudaGetLastError();
+  }
+  static cudaError_t eq_vjp(const SweepArgs& a, const double* rho0, const double* u0, const void* lam, double* g,
+                            cudaStream_t s) {
+    k_eq_vjp<L, T><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, rho0, u0, (const T*)lam, g);
+    return cudaGetLastError();
+  }
+};
+
+template <class L>
+cudaError_t launch_link_mask(const SweepArgs& a, uint32_t* mask, unsigned* types, cudaStream_t s) {
+  k_link_mask<L><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, mask, types);
+  return cudaGetLastError();
+}
+
+// Dispatch table of one (stencil, storage) pair.  Each lbm_inst_*.cu defines
+// one factory returning it, so the C ABI unit instantiates no kernels.
+struct OpsTable {
+  cudaError_t (*sweep)(int, int, bool, const SweepArgs&, cudaStream_t);
+  cudaError_t (*populations)(int, const SweepArgs&, double*, cudaStream_t);
+  cudaError_t (*macroscopic)(int, const SweepArgs&, void*, void*, bool, cudaStream_t);
+  cudaError_t (*reduce_partial)(int, const SweepArgs&, double*, int, cudaStream_t);
+  cudaError_t (*set_state)(bool, int, const SweepArgs&, const double*, const double*, const double*, cudaStream_t);
+  cudaError_t (*link_mask)(const SweepArgs&, uint32_t*, unsigned*, cudaStream_t);
+  cudaError_t (*adjoint)(int, bool, const SweepArgs&, const void*, void*, double*, cudaStream_t);
+  cudaError_t (*ke_seed)(bool, const SweepArgs&, const int*, double*, void*, double*, cudaStream_t);
+  cudaError_t (*eq_vjp)(const SweepArgs&, const double*, const double*, const void*, double*, cudaStream_t);
+};
+
+template <class L, class ST>
+OpsTable make_table() {
+  return OpsTable{&Ops<L, ST>::sweep,          &Ops<L, ST>::populations, &Ops<L, ST>::macroscopic,
+                  &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>,
+                  &Ops<L, ST>::adjoint,        &Ops<L, ST>::ke_seed,     &Ops<L, ST>::eq_vjp};
+}
+
+#define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();
+#define LBM_ALL_TABLES(X) \
+  X(d2q9, f64) X(d2q9, f32) X(d2q9, f16s) X(d2q9, f32s) \
+  X(d3q19, f64) X(d3q19, f32) X(d3q19, f16s) X(d3q19, f32s) \
+  X(d3q27, f64) X(d3q27, f32) X(d3q27, f16s) X(d3q27, f32s)
+LBM_ALL_TABLES(LBM_TABLE_DECL)
+
+
+}  // namespace lbm

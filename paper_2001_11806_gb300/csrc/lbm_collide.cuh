@@ -250,28 +250,132 @@ __device__ __forceinline__ void mrt_transpose_back(const T (&d)[L::Q], T (&nu)[L
   ((nu[Qs] = mrt_col<L, T, Qs>(d, std::make_integer_sequence<int, L::Q>{})), ...);
 }
 
+// Pair form of Eq. mrt.  Every row of the w-orthogonal basis is an even or an
+// odd polynomial (Gram-Schmidt never mixes parities, checked at compile time
+// below), so for a pair (q, qbar) the even rows see only g_q + g_qbar and the
+// odd rows only g_q - g_qbar; the back transform gives E + O for q and E - O
+// for qbar.  This halves both transforms.
+template <class L, int K>
+constexpr int mrt_odd = mrt::Table<L>::B.order[K] % 2;
+
+template <class L>
+constexpr bool mrt_parity_ok() {
+  for (int k = 0; k < L::Q; ++k) {
+    const int sgn = mrt::Table<L>::B.order[k] % 2 ? -1 : 1;
+    for (int q = 1; q < L::Q; q += 2)
+      if (mrt::Table<L>::B.M[k][q] != sgn * mrt::Table<L>::B.M[k][q + 1]) return false;
+    if (sgn < 0 && mrt::Table<L>::B.M[k][0] != 0) return false;
+  }
+  return true;
+}
+
+// m_K for one row from the rest value g0 and the pair sums / differences
+template <class L, class T, int K, int... Ps>
+__device__ __forceinline__ T mrt_row_pairs(T g0, const T (&gs)[(L::Q - 1) / 2], const T (&gd)[(L::Q - 1) / 2],
+                                           std::integer_sequence<int, Ps...>) {
+  T acc = mrt_odd<L, K> ? T(0) : mrt_acc<L, T, K, 0>(T(0), g0);
+  if constexpr (mrt_odd<L, K>) ((acc = mrt_acc<L, T, K, 2 * Ps + 1>(acc, gd[Ps])), ...);
+  else ((acc = mrt_acc<L, T, K, 2 * Ps + 1>(acc, gs[Ps])), ...);
+  return acc;
+}
+
+template <class L, class T, int K>
+__device__ __forceinline__ T mrt_delta_pairs(T g0, const T (&gs)[(L::Q - 1) / 2], const T (&gd)[(L::Q - 1) / 2],
+                                             const CollideParams& p) {
+  if constexpr (mrt_group<L, K> < 0) return T(0);
+  else return mrt_factor<T>(p, K) * mrt_row_pairs<L, T, K>(g0, gs, gd, std::make_integer_sequence<int, (L::Q - 1) / 2>{});
+}
+
+// sum over the non-conserved rows of one parity of M_K,Qi * d_K
+template <class L, class T, int ODD, int Qi, int K>
+__device__ __forceinline__ T mrt_acc_par(T acc, T d) {
+  if constexpr (mrt_group<L, K> < 0 || mrt_odd<L, K> != ODD) return acc;
+  else return mrt_acc<L, T, K, Qi>(acc, d);
+}
+
+template <class L, class T, int ODD, int Qi, int... Ks>
+__device__ __forceinline__ T mrt_col_par(const T (&d)[L::Q], std::integer_sequence<int, Ks...>) {
+  T acc = T(0);
+  ((acc = mrt_acc_par<L, T, ODD, Qi, Ks>(acc, d[Ks])), ...);
+  return acc;
+}
+
+template <class L, class T, int... Ks>
+__device__ __forceinline__ void mrt_forward_pairs(T g0, const T (&gs)[(L::Q - 1) / 2], const T (&gd)[(L::Q - 1) / 2],
+                                                  T (&d)[L::Q], const CollideParams& p,
+                                                  std::integer_sequence<int, Ks...>) {
+  ((d[Ks] = mrt_delta_pairs<L, T, Ks>(g0, gs, gd, p)), ...);
+}
+
+template <class L, class T, int... Ps>
+__device__ __forceinline__ void mrt_backward_pairs(T (&h)[L::Q], const T (&d)[L::Q], const T (&Gs)[(L::Q - 1) / 2],
+                                                   const T (&Gd)[(L::Q - 1) / 2], std::integer_sequence<int, Ps...>) {
+  constexpr auto ks = std::make_integer_sequence<int, L::Q>{};
+  (([&] {
+     constexpr int q = 2 * Ps + 1;
+     const T E = mrt_col_par<L, T, 0, q>(d, ks);
+     const T O = mrt_col_par<L, T, 1, q>(d, ks);
+     const T w = T(L::w(q));
+     h[q] = h[q] + Gs[Ps] + Gd[Ps] - w * (E + O);
+     h[q + 1] = h[q + 1] + Gs[Ps] - Gd[Ps] - w * (E - O);
+   }()),
+   ...);
+}
+
 template <class L, class T>
 __device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p) {
-  const Macro<L, T> m = macro_from_h<L, T>(h, p);
-  const T usq15 = T(1.5) * (m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2]);
-  const T uF3 = T(3) * (m.u[0] * m.F[0] + m.u[1] * m.F[1] + m.u[2] * m.F[2]);
-  T g[L::Q], G[L::Q];
+  static_assert(mrt_parity_ok<L>(), "basis rows must be even or odd polynomials");
+  constexpr int NP = (L::Q - 1) / 2;
+  T s[NP], dd[NP];
+  T drho = h[0], jx = T(0), jy = T(0), jz = T(0);
+  bool ix = false, iy = false, iz = false;
 #pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    T ev, od;
-    heq_parts<L, T>(q, m, usq15, ev, od);
-    g[q] = h[q] - (ev + od);  // h^eq_q = even + odd part for direction q
-    G[q] = T(0);
-    if (p.has_force) {
-      T se, so;
-      guo_parts<L, T>(q, m, uF3, se, so);
-      G[q] = se + so;
-      g[q] += T(0.5) * G[q];
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    s[k] = h[q] + h[q + 1];
+    dd[k] = h[q] - h[q + 1];
+    drho += s[k];
+    acc_signed(jx, ix, L::cx(q), dd[k]);
+    acc_signed(jy, iy, L::cy(q), dd[k]);
+    acc_signed(jz, iz, L::cz(q), dd[k]);
+  }
+  T F[3] = {T(0), T(0), T(0)};
+  const bool force = p.has_force != 0;
+  if (force) {
+    F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
+    jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
+  }
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
+  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T base = drho - T(1.5) * rho0 * usq;
+  const T k45 = T(4.5) * rho0, k3 = T(3) * rho0;
+  const T uF3 = T(3) * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
+  // g = h - h^eq + G/2 as rest value, pair sums and pair differences;
+  // G+ (even part) and G- (odd part) of the Guo source per pair
+  T G0 = T(0), Gs[NP], Gd[NP], gs[NP], gd[NP];
+  if (force) G0 = -T(L::w(0)) * uF3;
+  const T g0 = h[0] - T(L::w(0)) * base + T(0.5) * G0;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    Gs[k] = T(0);
+    Gd[k] = T(0);
+    if (force) {
+      const T cF = cdot<L, T>(q, F);
+      Gs[k] = w * (T(9) * cu * cF - uF3);
+      Gd[k] = w * T(3) * cF;
     }
+    gs[k] = s[k] - T(2) * w * fma(k45, cu * cu, base) + Gs[k];
+    gd[k] = dd[k] - T(2) * w * k3 * cu + Gd[k];
   }
   T d[L::Q];
-  mrt_forward<L, T>(g, d, p, std::make_integer_sequence<int, L::Q>{});
-  mrt_backward<L, T>(h, d, G, std::make_integer_sequence<int, L::Q>{});
+  mrt_forward_pairs<L, T>(g0, gs, gd, d, p, std::make_integer_sequence<int, L::Q>{});
+  h[0] = h[0] + G0 - T(L::w(0)) * mrt_col_par<L, T, 0, 0>(d, std::make_integer_sequence<int, L::Q>{});
+  mrt_backward_pairs<L, T>(h, d, Gs, Gd, std::make_integer_sequence<int, NP>{});
 }
 
 }  // namespace lbm

@@ -282,16 +282,24 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
         }
       }
     }
+    if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) {
-      const int p = opp(q);
-      if constexpr (KIND == K_AA_EVEN) {
-        reinterpret_cast<S*>(a.dstq[p])[cell] = D::store(v[q], L::w(q));
-      } else {
+      for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
+    } else {
+      // The neighbour offsets of the stores are rebuilt from a fresh read of
+      // %tid.x: an asm with side effects is not moved above the loads and its
+      // result cannot be merged with the offsets of the load phase, so the
+      // offsets are not held in registers across the collision.
+      int tx;
+      asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+      const Nbr nbs = make_nbr(a.g, blockIdx.x * blockDim.x + tx, y, z);
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) {
         // AA odd: fluid destination -> A[q][x + c_q]; boundary -> A[p][x]
+        const int p = opp(q);
         const bool b = BND && ((mask >> p) & 1u);
         const int qd = b ? p : q;
-        const int idx = b ? cell : nb.at(L::cx(q), L::cy(q), L::cz(q));
+        const int idx = b ? cell : nbs.at(L::cx(q), L::cy(q), L::cz(q));
         reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
       }
     }
@@ -370,7 +378,8 @@ __device__ __forceinline__ void moments_f64(const double (&f)[L::Q], const Colli
   }
   if (p.has_force) for (int d = 0; d < 3; ++d) j[d] += 0.5 * p.F[d];
   rho0 = p.incompressible ? 1.0 : rho;
-  for (int d = 0; d < 3; ++d) u[d] = j[d] / rho0;
+  const double inv = 1.0 / rho0;
+  for (int d = 0; d < 3; ++d) u[d] = j[d] * inv;
   if (L::D == 2) u[2] = 0.0;
 }
 
@@ -520,10 +529,24 @@ __device__ __forceinline__ double state_value(const double* P, const double* rho
   return L::w(q) * (r + r0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
 }
 
+// h_q = f^eq_q - w_q of the equilibrium at cell s, in the compute type T
+// (rho - 1 is formed in FP64 first so that shifted storage keeps it exactly).
+template <class L, class T>
+__device__ __forceinline__ T eq_dev(const double* rho, const double* u, long long N, int q, long long s,
+                                    int incompressible) {
+  const T dr = T(rho[s] - 1.0);
+  const T r0 = incompressible ? T(1) : T(1) + dr;
+  const T ux = T(u[s]), uy = T(u[N + s]), uz = L::D == 3 ? T(u[2 * N + s]) : T(0);
+  const T cu = T(L::cx(q)) * ux + T(L::cy(q)) * uy + T(L::cz(q)) * uz;
+  const T usq = ux * ux + uy * uy + uz * uz;
+  return T(L::w(q)) * (dr + r0 * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+}
+
 template <class L, class ST>
 __global__ void k_set_state(const SweepArgs a, int aa, int src_kind, const double* P, const double* rho,
                             const double* u) {
   using S = typename ST::S;
+  using T = typename ST::T;
   S* A = static_cast<S*>(a.dst);
   const long long N = a.g.N;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
@@ -531,7 +554,8 @@ __global__ void k_set_state(const SweepArgs a, int aa, int src_kind, const doubl
     const uint32_t mask = a.mask ? a.mask[cell] : 0u;
     if (!aa || (mask & MASK_SOLID)) {
       for (int q = 0; q < L::Q; ++q)
-        A[q * N + cell] = ST::from_f64(state_value<L>(P, rho, u, src_kind, N, q, cell, a.cp), L::w(q));
+        A[q * N + cell] = src_kind == 0 ? ST::from_f64(P[q * N + cell], L::w(q))
+                                        : ST::from_h(eq_dev<L, T>(rho, u, N, q, cell, a.cp.incompressible), L::w(q));
       continue;
     }
     int x, y, z;
@@ -569,7 +593,11 @@ __global__ void k_set_state(const SweepArgs a, int aa, int src_kind, const doubl
         }
       } else {
         const long long s = nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
-        v = state_value<L>(P, rho, u, src_kind, N, q, s, a.cp);
+        if (src_kind == 1) {
+          A[q * N + cell] = ST::from_h(eq_dev<L, T>(rho, u, N, q, s, a.cp.incompressible), L::w(q));
+          continue;
+        }
+        v = P[q * N + s];
       }
       A[q * N + cell] = ST::from_f64(v, L::w(q));
     }

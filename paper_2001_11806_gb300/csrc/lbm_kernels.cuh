@@ -306,6 +306,88 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
   }
 }
 
+// ---------------------------------------------------- FP16 two-cell sweep
+// Periodic FP16-shifted sweeps with two cells (x0, x0 + 1) per thread.  A
+// 2-byte population leaves a warp request at 64 B, so one cell per thread
+// keeps too few bytes in flight; here the two cells' populations of each
+// direction sit packed in one __half2 register, directions with c_x = 0 move
+// both cells with one aligned 32-bit access, the others with two 16-bit
+// accesses.  Each cell is unpacked, collided and repacked in turn, so the
+// register cost is one packed register per direction plus one collision.
+// Requires an even nx (x0 and every row start are then 4-byte aligned).
+template <class L, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
+  using T = float;
+  const int tp = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x0 = 2 * tp;
+  if (x0 >= a.g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int cell = x0 + a.g.nx * (y + a.g.ny * z);
+  const int nx = a.g.nx;
+  const int sy = nx, sz = nx * a.g.ny;
+  const int yo[3] = {(y == 0 ? a.g.ny - 1 : y - 1) * sy, y * sy, (y == a.g.ny - 1 ? 0 : y + 1) * sy};
+  const int zo[3] = {(z == 0 ? a.g.nz - 1 : z - 1) * sz, z * sz, (z == a.g.nz - 1 ? 0 : z + 1) * sz};
+  // x of the neighbours of cell 0 (x0) and cell 1 (x0 + 1) for dx = -1, 0, 1
+  const int xa[3] = {x0 == 0 ? nx - 1 : x0 - 1, x0, x0 + 1};
+  const int xb[3] = {x0, x0 + 1, x0 + 2 == nx ? 0 : x0 + 2};
+  __half2 P[L::Q];
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    // pull / AA even read direction q; AA odd reads slot qbar
+    const int qs = KIND == K_AA_ODD ? opp(q) : q;
+    const __half* base = reinterpret_cast<const __half*>(a.srcq[qs]);
+    if constexpr (KIND == K_AA_EVEN) {
+      P[q] = *reinterpret_cast<const __half2*>(base + cell);
+    } else {
+      const int dx = -L::cx(q), dy = -L::cy(q), dz = -L::cz(q);
+      const int row = yo[dy + 1] + zo[dz + 1];
+      if (dx == 0) P[q] = *reinterpret_cast<const __half2*>(base + row + x0);
+      else P[q] = __halves2half2(base[row + xa[dx + 1]], base[row + xb[dx + 1]]);
+    }
+  }
+  T v[L::Q];
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
+  collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    P[q] = __halves2half2(__float2half_rn(v[q]), __high2half(P[q]));
+    v[q] = __high2float(P[q]);
+  }
+  collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__low2half(P[q]), __float2half_rn(v[q]));
+  if constexpr (KIND == K_PULL) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.dstq[q]) + cell) = P[q];
+  } else if constexpr (KIND == K_AA_EVEN) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q)
+      *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.dstq[opp(q)]) + cell) = P[q];
+  } else {
+    // rebuild the neighbour offsets from a fresh %tid.x read (see k_sweep)
+    int tx;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+    const int x1 = 2 * (blockIdx.x * blockDim.x + tx);
+    const int yo2[3] = {(y == 0 ? a.g.ny - 1 : y - 1) * sy, y * sy, (y == a.g.ny - 1 ? 0 : y + 1) * sy};
+    const int zo2[3] = {(z == 0 ? a.g.nz - 1 : z - 1) * sz, z * sz, (z == a.g.nz - 1 ? 0 : z + 1) * sz};
+    const int xa2[3] = {x1 == 0 ? nx - 1 : x1 - 1, x1, x1 + 1};
+    const int xb2[3] = {x1, x1 + 1, x1 + 2 == nx ? 0 : x1 + 2};
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      __half* base = reinterpret_cast<__half*>(a.dstq[q]);
+      const int dx = L::cx(q), dy = L::cy(q), dz = L::cz(q);
+      const int row = yo2[dy + 1] + zo2[dz + 1];
+      if (dx == 0) {
+        *reinterpret_cast<__half2*>(base + row + x1) = P[q];
+      } else {
+        base[row + xa2[dx + 1]] = __low2half(P[q]);
+        base[row + xb2[dx + 1]] = __high2half(P[q]);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------- gather (FP64)
 // Populations f(x) of the current time in FP64 (unshifted).
 template <class L, class ST>
@@ -616,6 +698,14 @@ inline dim3 sweep_grid(const Geom& g) {
 
 template <class L, class ST, int OP, int KIND>
 cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
+  if constexpr (ST::ID == StF16S::ID) {
+    if (!bnd && (a.g.nx % 2) == 0) {
+      Geom half = a.g;
+      half.nx = a.g.nx / 2;
+      k_sweep_h2<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if (bnd)
     k_sweep<L, ST, OP, KIND, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
   else

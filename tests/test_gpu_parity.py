@@ -260,3 +260,18 @@ def test_poiseuille_exact_on_gpu():
         y = np.arange(1, H + 1)
         exact = F / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
         assert np.abs(u[1:H + 1, :] - exact[:, None]).max() / exact.max() < 1e-10
+
+
+@pytest.mark.parametrize("stencil,collision", [("D2Q9", "trt"), ("D3Q19", "trt"), ("D3Q19", "mrt"),
+                                               ("D3Q27", "srt"), ("D3Q27", "cumulant")])
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("nx", [534, 151])
+def test_f16_two_cell_kernel_parity(stencil, collision, pattern, nx):
+    """Periodic FP16-shifted runs with even nx use the two-cells-per-thread
+    kernel (534 = 267 cell pairs: two full 128-thread tiles and a ragged
+    tail); odd nx falls back to one cell per thread."""
+    shape = (nx, 3, 1) if stencil == "D2Q9" else (nx, 3, 2)
+    for steps in (3, 4):
+        r = run_pair(stencil, collision, "f16s", pattern, shape, steps)
+        ef, er, eu = _errs(r)
+        assert ef < 5e-3 and er < 5e-3 and eu < 5e-3, (steps, ef, er, eu)

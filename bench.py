@@ -8,6 +8,11 @@ larger than the 129 MB L2, so no flush is needed between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+The line also carries "variants" (the other workloads of the metric: two-grid
+pull, FP16-shifted storage, the MRT channel, the D3Q27 cumulant, D2Q9 FP64 and
+the adjoint step against the forward step) and "accuracy" (FP32 and
+FP16-shifted storage against an FP64 run of the same kernels).
+
 --impl reference times the FP64 numpy oracle on the host cores on a bounded
 sample of the same workload (a 32^3 periodic box per step).  Under torchrun
 (N > 1) every rank runs its own replica (weak scaling, no collective on the
@@ -204,6 +209,137 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _time_steps(sim, steps, torch):
+    stream = torch.cuda.current_stream(sim.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(sim.device)
+    return e0.elapsed_time(e1) / steps
+
+
+def run_variants(device, peak):
+    """The other workloads of the metric, one line each: MLUPS over all cells,
+    algorithmic GB/s (2 q sizeof per fluid cell, plus the 4 B link mask per
+    cell when boundaries are present) and its fraction of the measured peak."""
+    import torch
+
+    from paper_2001_11806_gb300 import inputs
+    from paper_2001_11806_gb300.sim import Sim
+    elem = {"f64": 8, "f32": 4, "f16s": 2}
+    out = []
+    specs = [
+        ("D3Q19 TRT FP32 256^3 two-grid pull", dict(stencil="D3Q19", collision="trt", storage="f32", pattern="pull",
+                                                  shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
+        ("D3Q19 TRT FP16-shifted 256^3 AA", dict(stencil="D3Q19", collision="trt", storage="f16s", pattern="aa",
+                                                 shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
+        ("D3Q19 MRT FP32 channel 512x128x128 AA", dict(stencil="D3Q19", collision="mrt", storage="f32", pattern="aa",
+                                                       shape=(512, 128, 128), omega=[1.7, 1.0, 1.0, 1.0],
+                                                       periodic=(False, False, False), u_wall=(0.05, 0, 0)),
+         "channel", 300),
+        ("D3Q19 MRT FP16-shifted channel 512x128x128 pull", dict(stencil="D3Q19", collision="mrt", storage="f16s",
+                                                                 pattern="pull", shape=(512, 128, 128),
+                                                                 omega=[1.7, 1.0, 1.0, 1.0],
+                                                                 periodic=(False, False, False), u_wall=(0.05, 0, 0)),
+         "channel", 300),
+        ("D3Q27 cumulant FP32 384^3 AA", dict(stencil="D3Q27", collision="cumulant", storage="f32", pattern="aa",
+                                              shape=(384,) * 3, omega=[1.95, 1.0, 1.0]), "tgv", 100),
+        ("D2Q9 SRT FP64 64^2 pull", dict(stencil="D2Q9", collision="srt", storage="f64", pattern="pull",
+                                         shape=(64, 64, 1), omega=[1.6]), "tgv2d", 2000),
+    ]
+    flags_channel = None
+    for name, kw, init, steps in specs:
+        flags = None
+        if init == "channel":
+            if flags_channel is None:
+                flags_channel = inputs.channel_flags(512, 128, 128)
+            flags = flags_channel
+        sim = Sim(device=device, flags=flags, **kw)
+        N, q = sim.N, sim.q
+        if init == "tgv":
+            rho, u = inputs.tgv3d(kw["shape"][0], U0, NOISE, SEED)
+        elif init == "tgv2d":
+            rho, u = inputs.tgv2d(64, 0.01)
+        else:
+            rho, u = np.ones(N), np.zeros((3, N))
+        sim.init_equilibrium(rho.reshape(-1), u.reshape(sim.d, -1))
+        sim.step(10)
+        ms = _time_steps(sim, steps, torch)
+        fluid = N if flags is None else int((flags == 0).sum())
+        nbytes = 2 * q * elem[kw["storage"]] * fluid + (4 * N if flags is not None else 0)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out.append({"workload": name, "mlups": round(N / ms / 1e3, 1),
+                    "fluid_mlups": round(fluid / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+                    "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    # adjoint step cost against the forward step (D3Q19 TRT FP32 128^3)
+    from paper_2001_11806_gb300 import _lib
+    sim = Sim("D3Q19", "trt", "f32", "pull", (128,) * 3, omega=[OMEGA_E], trt_magic=MAGIC, force=[1e-6, 0, 0],
+              device=device)
+    rho, u = inputs.tgv3d(128, U0, NOISE, SEED)
+    sim.init_equilibrium(rho.reshape(-1), u.reshape(3, -1))
+    sim.step(10)
+    fwd = _time_steps(sim, 200, torch)
+    raw, _ = sim.get_pdfs()
+    lam = [torch.zeros((19, sim.N), dtype=torch.float32, device=device) for _ in range(2)]
+    dF = torch.zeros(3, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(sim.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(5):
+        _lib.lib().lbm_adjoint_step(sim.ctx, raw.data_ptr(), lam[i % 2].data_ptr(), lam[1 - i % 2].data_ptr(),
+                                    dF.data_ptr())
+    e0.record(stream)
+    for i in range(200):
+        _lib.lib().lbm_adjoint_step(sim.ctx, raw.data_ptr(), lam[i % 2].data_ptr(), lam[1 - i % 2].data_ptr(),
+                                    dF.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    adj = e0.elapsed_time(e1) / 200
+    gbs = 3 * 19 * 4 * sim.N / (adj * 1e-3) / 1e9
+    out.append({"workload": "D3Q19 TRT FP32 128^3 adjoint step", "ms_per_step": round(adj, 4),
+                "forward_ms_per_step": round(fwd, 4), "adjoint_over_forward": round(adj / fwd, 3),
+                "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+    sim.close()
+    return out
+
+
+def run_accuracy(device):
+    """FP32 and FP16-shifted storage against an FP64 run of the same kernels
+    (the secondary reference; the FP64 oracle is too slow at this size):
+    D3Q19 TRT 256^3 TGV, 1000 steps, AA.  Relative L2 over all cells of
+    rho - 1 and of u, and the kinetic energy ratio E(T)/E(0)."""
+    import torch
+
+    from paper_2001_11806_gb300 import inputs
+    from paper_2001_11806_gb300.sim import Sim
+    n, T = N_SIDE, 1000
+    rho, u = inputs.tgv3d(n, U0, NOISE, SEED)
+    fields, ke = {}, {}
+    for st in ["f64", "f32", "f16s"]:
+        sim = Sim("D3Q19", "trt", st, "aa", (n,) * 3, omega=[OMEGA_E], trt_magic=MAGIC, device=device)
+        sim.init_equilibrium(rho.reshape(-1), u.reshape(3, -1))
+        e0 = sim.reduce()[4]
+        sim.step(T)
+        ke[st] = sim.reduce()[4] / e0
+        r, v = sim.macroscopic(True)
+        fields[st] = (r.cpu().numpy(), v.cpu().numpy())
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    r64, u64 = fields["f64"]
+    out = {"workload": "D3Q19 TRT 256^3 TGV u0 = 0.02, 1000 steps, AA; reference: FP64 GPU run",
+           "ke_ratio_f64": round(float(ke["f64"]), 8)}
+    for st in ["f32", "f16s"]:
+        r, v = fields[st]
+        out[st] = {"rho_minus_1": float(np.linalg.norm(r - r64) / np.linalg.norm(r64 - 1.0)),
+                   "u": float(max(np.linalg.norm(v[a] - u64[a]) / np.linalg.norm(u64[a]) for a in range(3))),
+                   "ke_ratio": round(float(ke[st]), 8)}
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -279,6 +415,8 @@ def run_gpu(args, world, rank, local):
         cpu_mlups, cpu_steps, cpu_dt = float("nan"), 0, 0.0
     else:
         cpu_mlups, cpu_steps, cpu_dt = oracle_sample_run(10 ** 9, 1, budget_s=12.0)
+    variants = None if args.no_variants else run_variants(device, peak)
+    accuracy = None if args.no_variants else run_accuracy(device)
     line = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
@@ -297,6 +435,8 @@ def run_gpu(args, world, rank, local):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
+        "variants": variants,
+        "accuracy": accuracy,
     }
     print(json.dumps(line))
     return 0
@@ -311,6 +451,7 @@ def main():
     # profiling aids: a smaller box of the same kernel, and skipping the CPU leg
     ap.add_argument("--size", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -447,6 +447,46 @@ __device__ void gather_f64(const SweepArgs& a, int view, int x, int y, int z, in
   }
 }
 
+// Shifted populations h = f - w of the current time in the compute type T
+// (same views and boundary values as gather_f64).
+template <class L, class ST>
+__device__ void gather_h(const SweepArgs& a, int view, int x, int y, int z, int cell, uint32_t mask,
+                         typename ST::T (&h)[L::Q]) {
+  using S = typename ST::S;
+  using T = typename ST::T;
+  const S* A = static_cast<const S*>(a.src);
+  const long long N = a.g.N;
+  const Nbr nb = make_nbr(a.g, x, y, z);
+  if (view == V_AA_NATURAL) {
+    for (int q = 0; q < L::Q; ++q) h[q] = ST::to_h(A[q * N + cell], L::w(q));
+    return;
+  }
+  if (view == V_AA_INVERTED) {
+    for (int q = 0; q < L::Q; ++q) {
+      if ((mask >> q) & 1u)
+        h[q] = ST::to_h(A[q * N + cell], L::w(q));
+      else
+        h[q] = ST::to_h(A[opp(q) * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q))], L::w(q));
+    }
+    return;
+  }
+  for (int q = 0; q < L::Q; ++q) {
+    const bool b = (mask >> q) & 1u;
+    h[q] = ST::to_h(A[(b ? opp(q) : q) * N + (b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q)))], L::w(q));
+  }
+  if (mask & MASK_SPECIAL) {
+    const OutletP op = outlet_params(a.cp);
+    for (int q = 1; q < L::Q; ++q) {
+      if ((mask >> q) & 1u) {
+        const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+        const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
+                                            L::cz(q) * a.cp.u_wall[2]);
+        h[q] = pull_special<L, ST, true>(A, N, cell, q, t, h[q], op, ubb);
+      }
+    }
+  }
+}
+
 template <class L>
 __device__ __forceinline__ void moments_f64(const double (&f)[L::Q], const CollideParams& p, double& rho,
                                             double& rho0, double (&u)[3]) {
@@ -502,14 +542,23 @@ __global__ void k_macroscopic(const SweepArgs a, int view, OUT* __restrict__ rho
       for (int d = 0; d < L::D; ++d) u_out[d * N + cell] = nan;
       continue;
     }
+    using T = typename ST::T;
     int x, y, z;
     cell_coords(a.g, cell, x, y, z);
-    double f[L::Q];
-    gather_f64<L, ST>(a, view, x, y, z, (int)cell, mask, f);
-    double rho, rho0, u[3];
-    moments_f64<L>(f, a.cp, rho, rho0, u);
-    rho_out[cell] = OUT(rho);
-    for (int d = 0; d < L::D; ++d) u_out[d * N + cell] = OUT(u[d]);
+    T h[L::Q];
+    gather_h<L, ST>(a, view, x, y, z, (int)cell, mask, h);
+    T drho = T(0), j[3] = {T(0), T(0), T(0)};
+    for (int q = 0; q < L::Q; ++q) {
+      drho += h[q];
+      j[0] += T(L::cx(q)) * h[q];
+      j[1] += T(L::cy(q)) * h[q];
+      j[2] += T(L::cz(q)) * h[q];
+    }
+    if (a.cp.has_force)
+      for (int d = 0; d < 3; ++d) j[d] += T(0.5 * a.cp.F[d]);
+    const T inv = T(1) / (a.cp.incompressible ? T(1) : T(1) + drho);
+    rho_out[cell] = OUT(1.0 + double(drho));
+    for (int d = 0; d < L::D; ++d) u_out[d * N + cell] = OUT(j[d] * inv);
   }
 }
 
@@ -595,94 +644,68 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsi
   }
 }
 
-// Initialisation / state upload.  src_kind 0: P from an FP64 array P[q][N];
-// src_kind 1: P = f^eq(rho[N], u[d][N]) (Eq. discrete_eq).  pattern K_PULL
-// writes P; pattern AA writes the natural (even-parity) layout, i.e. the
-// streamed populations f_q(x) = P_q(x - c_q), or B_q(P(x)) on boundary links.
-template <class L>
-__device__ __forceinline__ double state_value(const double* P, const double* rho, const double* u, int src_kind,
-                                              long long N, int q, long long cell, const CollideParams& p) {
-  if (src_kind == 0) return P[q * N + cell];
-  const double r = rho[cell];
-  const double r0 = p.incompressible ? 1.0 : r;
-  double uu[3] = {u[cell], u[N + cell], L::D == 3 ? u[2 * N + cell] : 0.0};
-  const double cu = L::cx(q) * uu[0] + L::cy(q) * uu[1] + L::cz(q) * uu[2];
-  const double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
-  return L::w(q) * (r + r0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
-}
-
-// h_q = f^eq_q - w_q of the equilibrium at cell s, in the compute type T
-// (rho - 1 is formed in FP64 first so that shifted storage keeps it exactly).
-template <class L, class T>
-__device__ __forceinline__ T eq_dev(const double* rho, const double* u, long long N, int q, long long s,
-                                    int incompressible) {
-  const T dr = T(rho[s] - 1.0);
-  const T r0 = incompressible ? T(1) : T(1) + dr;
-  const T ux = T(u[s]), uy = T(u[N + s]), uz = L::D == 3 ? T(u[2 * N + s]) : T(0);
-  const T cu = T(L::cx(q)) * ux + T(L::cy(q)) * uy + T(L::cz(q)) * uz;
-  const T usq = ux * ux + uy * uy + uz * uz;
-  return T(L::w(q)) * (dr + r0 * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
-}
-
-template <class L, class ST>
-__global__ void k_set_state(const SweepArgs a, int aa, int src_kind, const double* P, const double* rho,
-                            const double* u) {
-  using S = typename ST::S;
+// Initialisation by push: every cell forms its own P(x) (from FP64 rho/u or
+// an FP64 P array) once and writes it where the layout needs it.  Pull
+// layout: P_q(x) into slot q of its own cell.  AA natural layout (even
+// parity): f_q(y) = P_q(y - c_q), so cell x pushes P_q(x) into slot q of
+// y = x + c_q, exactly like the stores of the odd step; when y is not fluid
+// the boundary value B_qbar(P(x)) goes to slot qbar of x instead.  Each slot
+// is written once; non-fluid cells write their own slots.
+template <class L, class ST, bool BND>
+__global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int aa, int src_kind, const double* P,
+                                                       const double* rho, const double* u) {
   using T = typename ST::T;
-  S* A = static_cast<S*>(a.dst);
+  using S = typename ST::S;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int cell = x + a.g.nx * (y + a.g.ny * z);
   const long long N = a.g.N;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
-       cell += (long long)gridDim.x * blockDim.x) {
-    const uint32_t mask = a.mask ? a.mask[cell] : 0u;
-    if (!aa || (mask & MASK_SOLID)) {
-      for (int q = 0; q < L::Q; ++q)
-        A[q * N + cell] = src_kind == 0 ? ST::from_f64(P[q * N + cell], L::w(q))
-                                        : ST::from_h(eq_dev<L, T>(rho, u, N, q, cell, a.cp.incompressible), L::w(q));
-      continue;
-    }
-    int x, y, z;
-    cell_coords(a.g, cell, x, y, z);
-    const Nbr nb = make_nbr(a.g, x, y, z);
-    double uP[3] = {0, 0, 0};
-    bool have_up = false;
+  uint32_t mask = 0;
+  if constexpr (BND) mask = a.mask[cell];
+  T v[L::Q];  // shifted populations h = P - w
+  if (src_kind == 0) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) v[q] = T(P[q * N + cell] - L::w(q));
+  } else {
+    const T dr = T(rho[cell] - 1.0);
+    const T r0 = a.cp.incompressible ? T(1) : T(1) + dr;
+    const T uu[3] = {T(u[cell]), T(u[N + cell]), L::D == 3 ? T(u[2 * N + cell]) : T(0)};
+    const T usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+#pragma unroll
     for (int q = 0; q < L::Q; ++q) {
-      double v;
-      if ((mask >> q) & 1u) {
-        const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
-        if (t == L_OUTLET) {
-          if (!have_up) {
-            double r = 0, j[3] = {0, 0, 0};
-            for (int k = 0; k < L::Q; ++k) {
-              const double pv = state_value<L>(P, rho, u, src_kind, N, k, cell, a.cp);
-              r += pv;
-              j[0] += L::cx(k) * pv; j[1] += L::cy(k) * pv; j[2] += L::cz(k) * pv;
-            }
-            if (a.cp.has_force) for (int d = 0; d < 3; ++d) j[d] -= 0.5 * a.cp.F[d];
-            const double r0 = a.cp.incompressible ? 1.0 : r;
-            for (int d = 0; d < 3; ++d) uP[d] = j[d] / r0;
-            if (L::D == 2) uP[2] = 0.0;
-            have_up = true;
-          }
-          const double ro = a.cp.rho_out;
-          const double ro0 = a.cp.incompressible ? 1.0 : ro;
-          const double cu = L::cx(q) * uP[0] + L::cy(q) * uP[1] + L::cz(q) * uP[2];
-          const double usq = uP[0] * uP[0] + uP[1] * uP[1] + uP[2] * uP[2];
-          v = L::w(q) * (ro + ro0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
-        } else {
-          v = state_value<L>(P, rho, u, src_kind, N, opp(q), cell, a.cp);
-          if (t == L_INLET)
-            v += 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] + L::cz(q) * a.cp.u_wall[2]);
-        }
-      } else {
-        const long long s = nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
-        if (src_kind == 1) {
-          A[q * N + cell] = ST::from_h(eq_dev<L, T>(rho, u, N, q, s, a.cp.incompressible), L::w(q));
-          continue;
-        }
-        v = P[q * N + s];
-      }
-      A[q * N + cell] = ST::from_f64(v, L::w(q));
+      const T cu = cdot<L, T>(q, uu);
+      v[q] = T(L::w(q)) * (dr + r0 * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
     }
+  }
+  if (!aa || (mask & MASK_SOLID)) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = ST::from_h(v[q], L::w(q));
+    return;
+  }
+  if constexpr (BND) {
+    if (mask & MASK_SPECIAL) {
+      const OutletP op = outlet_params(a.cp);
+      T up[3];
+      post_velocity<L, T, true>(v, op, up);
+      for (int q = 1; q < L::Q; ++q) {
+        const int p = opp(q);
+        if ((mask >> p) & 1u) {
+          const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+          if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
+          else if (t == L_OUTLET) v[q] = outlet_value<L, T, true>(p, up, op);
+        }
+      }
+    }
+  }
+  const Nbr nb = make_nbr(a.g, x, y, z);
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    const int p = opp(q);
+    const bool b = BND && ((mask >> p) & 1u);
+    const int qd = b ? p : q;
+    const int idx = b ? cell : nb.at(L::cx(q), L::cy(q), L::cz(q));
+    reinterpret_cast<S*>(a.dstq[qd])[idx] = ST::from_h(v[q], L::w(q));
   }
 }
 

@@ -38,7 +38,10 @@ struct Ops {
   }
   static cudaError_t set_state(bool aa, int src_kind, const SweepArgs& a, const double* P, const double* rho,
                                const double* u, cudaStream_t s) {
-    k_set_state<L, ST><<<grid_stride_blocks(a.g.N, 128), 128, 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
+    if (a.mask != nullptr)
+      k_init_push<L, ST, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
+    else
+      k_init_push<L, ST, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
     return cudaGetLastError();
   }
   using T = typename ST::T;

@@ -16,6 +16,8 @@ u have shape (d, ...cells).  Everything works for float64 and for complex128
   f*_q = f_q - omega_e (f+_q - feq+_q) - omega_o (f-_q - feq-_q).
 - MRT, Eq. mrt: f* = M^-1 [S m^eq + (I - S) M f] with m^eq = M f^eq, the
   basis and rates of moments.weighted_orthogonal_basis / relaxation_rates.
+- Smagorinsky (Sec. III-C, turbulence models): per-cell omega from Pi^neq,
+  see smagorinsky_omega.
 - Guo forcing: raw source G_q = w_q [(c_q - u)/cs2 + (c_q.u) c_q/cs2^2].F;
   SRT adds (1 - omega/2) G, TRT adds (1 - omega_e/2) G+ + (1 - omega_o/2) G-,
   MRT adds M^-1 (I - S/2) M G.
@@ -85,20 +87,45 @@ def trt_odd_rate(omega_e, magic):
     return 1.0 / (magic / (1.0 / omega_e - 0.5) + 0.5)
 
 
+def smagorinsky_omega(lat, f, feq, rho, omega0, cs):
+    """Per-cell relaxation rate of the Smagorinsky model (Sec. III-C,
+    "Turbulence models"): nu = nu_0 + (C_S Delta)^2 |S| with Delta = 1,
+    |S| = sqrt(2 S_ij S_ij), S_ij = -(3 omega / (2 rho)) Pi^neq_ij,
+    Pi^neq_ij = sum_q c_qi c_qj (f_q - f^eq_q), omega = 2 / (6 C_S^2 |S| + 6 nu_0 + 1).
+    With P = sqrt(2 Pi^neq : Pi^neq) the pair is solved for tau = 1/omega:
+    2 tau^2 - 2 tau_0 tau - 9 C_S^2 P / rho = 0 (positive root)."""
+    c = lat.c.astype(np.float64)
+    fneq = f - feq
+    pp = 0.0
+    for a in range(lat.d):
+        for b in range(lat.d):
+            pab = np.tensordot(c[:, a] * c[:, b], fneq, axes=([0], [0]))
+            pp = pp + pab * pab
+    P = np.sqrt(2.0 * pp)
+    tau0 = 1.0 / omega0
+    tau = 0.5 * (tau0 + np.sqrt(tau0 * tau0 + 18.0 * cs * cs * P / rho))
+    return 1.0 / tau
+
+
 class Method:
     """A collision operator with its parameters.
 
     op: 'srt' (omegas=[omega]), 'trt' ([omega_e, omega_o]), 'mrt'
     ([omega_shear, omega_bulk, omega_3, omega_4(, omega_5, omega_6)]) or
     'cumulant' ([omega_shear, omega_bulk, omega_higher]).
+    cs > 0 adds the Smagorinsky model to SRT/TRT: the (even) rate becomes the
+    per-cell smagorinsky_omega; with magic set, the TRT odd rate follows it
+    through Lambda = magic, otherwise omega_o stays as given.
     """
 
-    def __init__(self, lat, op, omegas, incompressible=False, force=None):
+    def __init__(self, lat, op, omegas, incompressible=False, force=None, cs=0.0, magic=None):
         self.lat = lat
         self.op = op
         self.omegas = list(omegas)
         self.incompressible = incompressible
         self.force = None if force is None else np.asarray(force)
+        self.cs = float(cs)
+        self.magic = magic
         if op == "mrt":
             basis = mo.weighted_orthogonal_basis(lat)
             Mx = mo.moment_matrix(basis, lat)
@@ -130,6 +157,21 @@ def collide(method, f):
     rho, u = velocity(lat, f, method.force, method.incompressible)
     feq = equilibrium(lat, rho, u, method.incompressible)
     G = guo_source(lat, u, method.force) if method.force is not None else None
+    if method.cs > 0.0 and method.op in ("srt", "trt"):
+        om = smagorinsky_omega(lat, f, feq, density(f), method.omegas[0], method.cs)
+        if method.op == "srt":
+            oo = om
+        elif method.magic is not None:
+            oo = 1.0 / (method.magic / (1.0 / om - 0.5) + 0.5)
+        else:
+            oo = method.omegas[1]
+        fp, fm = _pm(lat, f)
+        ep, em = _pm(lat, feq)
+        out = f - om * (fp - ep) - oo * (fm - em)
+        if G is not None:
+            gp, gm = _pm(lat, G)
+            out = out + (1 - om / 2) * gp + (1 - oo / 2) * gm
+        return out
     if method.op == "srt":
         om = method.omegas[0]
         out = f + om * (feq - f)

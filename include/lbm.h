@@ -107,6 +107,10 @@ typedef struct lbm_params {
   double u_wall[3];     /* velocity of INLET (UBB) links, rho_0 = 1 */
   double rho_outlet;    /* density of OUTLET links: B_q = f^eq_q(rho_outlet, u_P(x)) */
   double force[3];      /* uniform body force, Guo scheme; zero = no force */
+  /* Smagorinsky constant C_S (filter width 1) for SRT/TRT; 0 = off.  The even
+   * rate becomes a per-cell omega from the non-equilibrium stress (Sec. III-C,
+   * turbulence models); with trt_magic the odd rate follows through Lambda. */
+  double smagorinsky_cs;
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;

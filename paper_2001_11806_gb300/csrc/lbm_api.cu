@@ -68,6 +68,7 @@ struct lbm_ctx {
   unsigned link_types = 0;  // OR of the boundary-link types present (L_INLET, L_OUTLET)
   cudaStream_t stream = nullptr;
   int64_t t = 0;
+  int kernel_op = 0;  // collision operator of the sweep kernels (LES variants included)
   CollideParams cp;
   OpsTable ops;
   std::string err;
@@ -154,6 +155,14 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(p->force[i]) || !std::isfinite(p->u_wall[i])) { *msg = "non-finite force or wall velocity"; return LBM_E_INVAL; }
   if (!(p->rho_outlet > 0.0) || !std::isfinite(p->rho_outlet)) { *msg = "rho_outlet must be > 0"; return LBM_E_INVAL; }
+  if (!(p->smagorinsky_cs >= 0.0) || !std::isfinite(p->smagorinsky_cs)) {
+    *msg = "smagorinsky_cs must be >= 0";
+    return LBM_E_INVAL;
+  }
+  if (p->smagorinsky_cs > 0.0 && (p->collision == LBM_MRT || p->collision == LBM_CUMULANT)) {
+    *msg = "the Smagorinsky model is built for SRT and TRT";
+    return LBM_E_UNSUPPORTED;
+  }
   return LBM_OK;
 }
 
@@ -207,6 +216,13 @@ void fill_collide_params(lbm_ctx* c) {
   if (c->d == 2) { cp.F[2] = 0.0; cp.u_wall[2] = 0.0; }
   cp.incompressible = p.incompressible ? 1 : 0;
   cp.rho_out = p.rho_outlet;
+  cp.smag = p.smagorinsky_cs > 0.0 ? 1 : 0;
+  cp.smag_magic = (p.collision == LBM_TRT && p.trt_magic) ? 1 : 0;
+  cp.smag_18cs2 = 18.0 * p.smagorinsky_cs * p.smagorinsky_cs;
+  cp.smag_tau0 = 1.0 / om[0];
+  cp.smag_lambda = p.magic;
+  c->kernel_op = p.collision;
+  if (cp.smag) c->kernel_op = p.collision == LBM_SRT ? OP_SRT_LES : OP_TRT_LES;
 }
 
 }  // namespace
@@ -338,11 +354,11 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     cudaError_t e;
     if (c->p.pattern == LBM_PULL) {
       SweepArgs a = make_args(c, c->buf[c->cur], c->buf[1 - c->cur]);
-      e = c->ops.sweep(c->p.collision, K_PULL, c->has_mask, a, c->stream);
+      e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
       if (e == cudaSuccess) c->cur = 1 - c->cur;
     } else {
       SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
-      e = c->ops.sweep(c->p.collision, (c->t & 1) ? K_AA_ODD : K_AA_EVEN, c->has_mask, a, c->stream);
+      e = c->ops.sweep(c->kernel_op, (c->t & 1) ? K_AA_ODD : K_AA_EVEN, c->has_mask, a, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "step");
     ++c->t;
@@ -431,7 +447,7 @@ lbm_status lbm_step_pull(lbm_ctx* c, const void* src, void* dst) {
   if (!c || !src || !dst || src == dst) return LBM_E_INVAL;
   if (c->p.pattern != LBM_PULL) return LBM_E_STATE;
   SweepArgs a = make_args(c, src, dst);
-  cudaError_t e = c->ops.sweep(c->p.collision, K_PULL, c->has_mask, a, c->stream);
+  cudaError_t e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "step_pull");
 }
 
@@ -447,6 +463,10 @@ lbm_status adjoint_ok(lbm_ctx* c) {
   }
   if (c->link_types & L_OUTLET) {
     c->err = "outlet links are not differentiated";
+    return LBM_E_UNSUPPORTED;
+  }
+  if (c->cp.smag) {
+    c->err = "the Smagorinsky model is not differentiated";
     return LBM_E_UNSUPPORTED;
   }
   return LBM_OK;

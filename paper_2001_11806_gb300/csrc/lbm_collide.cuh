@@ -21,7 +21,8 @@
 
 namespace lbm {
 
-enum Op : int { OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3 };
+// OP_SRT_LES / OP_TRT_LES: SRT / TRT with the Smagorinsky model compiled in
+enum Op : int { OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3, OP_SRT_LES = 4, OP_TRT_LES = 5 };
 
 // Runtime parameters of a sweep, passed by value to the kernel.
 struct CollideParams {
@@ -34,6 +35,10 @@ struct CollideParams {
   int incompressible;
   double u_wall[3];
   double rho_out;
+  // Smagorinsky model (SRT/TRT): 18 C_S^2, tau_0 = 1/omega_0, magic Lambda
+  int smag;
+  int smag_magic;
+  double smag_18cs2, smag_tau0, smag_lambda;
 };
 
 template <class T> __device__ __forceinline__ T rate(const CollideParams& p, int i);
@@ -160,8 +165,35 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0;
-  const T oe = rate<T>(p, 0);
-  const T oo = OP == OP_SRT ? oe : rate<T>(p, 1);
+  constexpr bool SRT = OP == OP_SRT || OP == OP_SRT_LES;
+  constexpr bool LES = OP == OP_SRT_LES || OP == OP_TRT_LES;
+  T oe = rate<T>(p, 0);
+  T oo = SRT ? oe : rate<T>(p, 1);
+  if constexpr (LES) {
+    // Smagorinsky (Sec. III-C): Pi^neq from the pair sums of g = h - h^eq
+    // (even in c, so only s - 2 h^eq+ enters); tau from the quadratic
+    // 2 tau^2 - 2 tau_0 tau - 9 C_S^2 sqrt(2 Pi:Pi) / rho = 0
+    T pxx = T(0), pyy = T(0), pzz = T(0), pxy = T(0), pxz = T(0), pyz = T(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int q = 2 * k + 1;
+      const T cu = cdot<L, T>(q, u);
+      const T g = s[k] - T(2.0 * L::w(q)) * fma(k45, cu * cu, base);
+      const int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
+      if (cx) pxx += g;
+      if (cy) pyy += g;
+      if (cz) pzz += g;
+      if (cx && cy) pxy += cx * cy > 0 ? g : -g;
+      if (cx && cz) pxz += cx * cz > 0 ? g : -g;
+      if (cy && cz) pyz += cy * cz > 0 ? g : -g;
+    }
+    const T P = sqrt(T(2) * (pxx * pxx + pyy * pyy + pzz * pzz + T(2) * (pxy * pxy + pxz * pxz + pyz * pyz)));
+    const T tau0 = T(p.smag_tau0);
+    const T tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + T(p.smag_18cs2) * P / (T(1) + drho)));
+    oe = T(1) / tau;
+    if (SRT) oo = oe;
+    else if (p.smag_magic) oo = T(1) / (T(p.smag_lambda) / (tau - T(0.5)) + T(0.5));
+  }
   const T c1 = T(0.5) - T(0.5) * oe, c2 = T(0.5) - T(0.5) * oo;
   const T m3o = T(3) * rho0 * oo;
   const T ge = T(1) - T(0.5) * oe, go = T(1) - T(0.5) * oo;

@@ -137,7 +137,7 @@ struct Dom {
 
 template <class ST, int OP>
 constexpr bool dom_h() {
-  return ST::shifted || !(OP == OP_SRT || OP == OP_TRT);
+  return ST::shifted || !(OP == OP_SRT || OP == OP_TRT || OP == OP_SRT_LES || OP == OP_TRT_LES);
 }
 
 // Outlet value f^eq_q(rho_out, u) in the register domain (minus w_q if DH).
@@ -194,6 +194,16 @@ __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, st
 template <class L, class T, bool DH>
 __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_TRT>) {
   collide_pairs<L, T, OP_TRT, DH>(v, p);
+}
+template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p,
+                                        std::integral_constant<int, OP_SRT_LES>) {
+  collide_pairs<L, T, OP_SRT_LES, DH>(v, p);
+}
+template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p,
+                                        std::integral_constant<int, OP_TRT_LES>) {
+  collide_pairs<L, T, OP_TRT_LES, DH>(v, p);
 }
 template <class L, class T, bool DH>
 __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_MRT>) {

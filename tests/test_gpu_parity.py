@@ -275,3 +275,31 @@ def test_f16_two_cell_kernel_parity(stencil, collision, pattern, nx):
         r = run_pair(stencil, collision, "f16s", pattern, shape, steps)
         ef, er, eu = _errs(r)
         assert ef < 5e-3 and er < 5e-3 and eu < 5e-3, (steps, ef, er, eu)
+
+
+@pytest.mark.parametrize("stencil", ["D2Q9", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("collision,magic", [("srt", None), ("trt", None), ("trt", 3 / 16)])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+def test_smagorinsky_parity(stencil, collision, magic, storage, pattern):
+    """Per-cell Smagorinsky rate (C_S = 0.17) on random populations with walls,
+    an inlet, an outlet and a body force."""
+    lat = olat.get(stencil)
+    shape = _shape(stencil)
+    fl = _flags(shape)
+    om = [1.7] if collision == "srt" else [1.7, 0.9]
+    force = [2e-4, -1e-4, 5e-5]
+    sim = Sim(stencil, collision, storage, pattern, shape, periodic=(False, False, True), omega=om,
+              trt_magic=magic, u_wall=(0.05, 0.0, 0.0), force=force, flags=fl, smagorinsky_cs=0.17)
+    P = inputs.random_pdfs(lat.w, shape[::-1], seed=12)
+    sim.set_state(P.reshape(lat.q, -1))
+    sim.step(3)
+    m = oco.Method(lat, collision, om, force=force[: lat.d], cs=0.17, magic=magic)
+    ref = olbm.Sim(m, shape, periodic=(False, False, True), flags=fl, u_wall=(0.05, 0.0, 0.0))
+    ref.P = P.copy()
+    ref.step(3)
+    fluid = fl.reshape(-1) == 0
+    fg = sim.populations().cpu().numpy()[:, fluid]
+    fr = ref.populations().reshape(lat.q, -1)[:, fluid]
+    err = np.linalg.norm(fg - fr) / np.linalg.norm(fr - lat.w[:, None])
+    assert err < TOL[storage], err

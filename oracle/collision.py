@@ -18,6 +18,8 @@ u have shape (d, ...cells).  Everything works for float64 and for complex128
   basis and rates of moments.weighted_orthogonal_basis / relaxation_rates.
 - Smagorinsky (Sec. III-C, turbulence models): per-cell omega from Pi^neq,
   see smagorinsky_omega.
+- Entropic KBC (Sec. III-C): collide_kbc, op 'kbc' with omegas [omega_s]
+  or [omega_s, omega_bulk]; omega_h per cell from the entropy condition.
 - Guo forcing: raw source G_q = w_q [(c_q - u)/cs2 + (c_q.u) c_q/cs2^2].F;
   SRT adds (1 - omega/2) G, TRT adds (1 - omega_e/2) G+ + (1 - omega_o/2) G-,
   MRT adds M^-1 (I - S/2) M G.
@@ -112,7 +114,8 @@ class Method:
 
     op: 'srt' (omegas=[omega]), 'trt' ([omega_e, omega_o]), 'mrt'
     ([omega_shear, omega_bulk, omega_3, omega_4(, omega_5, omega_6)]) or
-    'cumulant' ([omega_shear, omega_bulk, omega_higher]).
+    'cumulant' ([omega_shear, omega_bulk, omega_higher]) or 'kbc'
+    ([omega_shear(, omega_bulk)], omega_h chosen per cell).
     cs > 0 adds the Smagorinsky model to SRT/TRT: the (even) rate becomes the
     per-cell smagorinsky_omega; with magic set, the TRT odd rate follows it
     through Lambda = magic, otherwise omega_o stays as given.
@@ -126,7 +129,7 @@ class Method:
         self.force = None if force is None else np.asarray(force)
         self.cs = float(cs)
         self.magic = magic
-        if op == "mrt":
+        if op in ("mrt", "kbc"):
             basis = mo.weighted_orthogonal_basis(lat)
             Mx = mo.moment_matrix(basis, lat)
             self.basis = basis
@@ -172,6 +175,8 @@ def collide(method, f):
             gp, gm = _pm(lat, G)
             out = out + (1 - om / 2) * gp + (1 - oo / 2) * gm
         return out
+    if method.op == "kbc":
+        return collide_kbc(method, f, feq)
     if method.op == "srt":
         om = method.omegas[0]
         out = f + om * (feq - f)
@@ -197,3 +202,47 @@ def collide(method, f):
             mstar = mstar + (1 - S / 2) * np.tensordot(M, G, axes=([1], [0]))
         return np.tensordot(Minv, mstar, axes=([1], [0]))
     raise ValueError(method.op)
+
+
+def kbc_parts(method, f, feq):
+    """(Delta s, Delta b, Delta h): the non-equilibrium part f - f^eq projected
+    onto the moment groups of the w-orthogonal MRT basis (Eq. mrt): shear
+    (the traceless second-order moments), bulk (the trace) and h (every
+    moment of order >= 3), so that f = f^eq + Delta s + Delta b + Delta h."""
+    M, Minv = method.M, method.Minv
+    kinds = [m.kind for m in method.basis]
+    m = np.tensordot(M, f - feq, axes=([1], [0]))
+    out = []
+    for group in (("shear",), ("bulk",), ("higher",)):
+        sel = np.array([1.0 if k in group else 0.0 for k in kinds]).reshape((-1,) + (1,) * (f.ndim - 1))
+        out.append(np.tensordot(Minv, sel * m, axes=([1], [0])))
+    return tuple(out)
+
+
+def kbc_omega_h(method, f, feq):
+    """omega_h from the paper's linearised optimality condition
+    sum_q Delta h_q f'_q / f^eq_q = 0 (Sec. III-C, entropic KBC), with
+    f' = f - omega_s Delta s - omega_b Delta b - omega_h Delta h:
+    omega_h = 1 + [(1 - omega_s) <Ds, Dh>_E + (1 - omega_b) <Db, Dh>_E] / <Dh, Dh>_E,
+    <a, b>_E = sum_q a_q b_q / f^eq_q.  For omega_b = omega_s this is
+    Eq. entropic_direct_omega_eq with Delta s + Delta b in the role of the
+    paper's Delta s.  Where <Dh, Dh>_E <= 1e-30 (no higher-order
+    deviation to tune) omega_h = 1."""
+    om_s, om_b = method.omegas[0], method.omegas[1] if len(method.omegas) > 1 else method.omegas[0]
+    ds, db, dh = kbc_parts(method, f, feq)
+    num = (1.0 - om_s) * (ds * dh / feq).sum(axis=0) + (1.0 - om_b) * (db * dh / feq).sum(axis=0)
+    den = (dh * dh / feq).sum(axis=0)
+    safe = den > 1e-30
+    return np.where(safe, 1.0 + num / np.where(safe, den, 1.0), 1.0), (ds, db, dh)
+
+
+def collide_kbc(method, f, feq):
+    """Entropic KBC (Sec. III-C, Eq. entropic_linear_update extended by a
+    fixed bulk rate): f' = f - omega_s Delta s - omega_b Delta b - omega_h Delta h,
+    omega_h per cell from kbc_omega_h.  omegas = [omega_s] or [omega_s, omega_b];
+    a body force is not defined for this operator."""
+    if method.force is not None:
+        raise ValueError("KBC collision with a body force is not defined here")
+    om_s, om_b = method.omegas[0], method.omegas[1] if len(method.omegas) > 1 else method.omegas[0]
+    om_h, (ds, db, dh) = kbc_omega_h(method, f, feq)
+    return f - om_s * ds - om_b * db - om_h * dh

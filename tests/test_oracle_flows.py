@@ -56,6 +56,8 @@ def _tgv3d_rate_error(name, op, omegas, n):
     ("D3Q19", "trt", [1.4, 1.4]),
     ("D3Q19", "mrt", [1.4, 1.0, 1.0, 1.0]),
     ("D3Q27", "cumulant", [1.4, 1.0, 1.0]),
+    ("D3Q19", "kbc", [1.4, 1.0]),
+    ("D3Q27", "kbc", [1.4]),
 ])
 def test_tgv3d_low_re_decay_second_order(name, op, omegas):
     """Decay rate -> 3 nu k^2 with second-order convergence (8^3 -> 16^3)."""

@@ -237,6 +237,10 @@ def run_variants(device, peak):
         ("D3Q19 SRT + Smagorinsky (C_S 0.17) FP32 256^3 AA",
          dict(stencil="D3Q19", collision="srt", storage="f32", pattern="aa", shape=(256,) * 3, omega=[1.95],
               smagorinsky_cs=0.17), "tgv", 300),
+        ("D3Q19 KBC FP32 256^3 AA", dict(stencil="D3Q19", collision="kbc", storage="f32", pattern="aa",
+                                         shape=(256,) * 3, omega=[1.95, 1.95]), "tgv", 300),
+        ("D3Q27 KBC FP32 256^3 AA", dict(stencil="D3Q27", collision="kbc", storage="f32", pattern="aa",
+                                         shape=(256,) * 3, omega=[1.95, 1.95]), "tgv", 200),
         ("D3Q19 MRT FP32 channel 512x128x128 AA", dict(stencil="D3Q19", collision="mrt", storage="f32", pattern="aa",
                                                        shape=(512, 128, 128), omega=[1.7, 1.0, 1.0, 1.0],
                                                        periodic=(False, False, False), u_wall=(0.05, 0, 0)),

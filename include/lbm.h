@@ -11,7 +11,8 @@
  *   - SRT/BGK (Eq. bgk), TRT (Sec. III-C), MRT with the weighted-orthogonal
  *     moment basis built from the monomial procedure of Sec. III-A (Eq. mrt),
  *     cumulant collision for D3Q27 (Sec. III-B, Eq.
- *     cumulant_generating_function);
+ *     cumulant_generating_function), the Smagorinsky model for SRT/TRT and
+ *     the entropic KBC operator (Sec. III-C);
  *   - two-array stream-pull-collide and single-array AA update patterns
  *     (Sec. IV-B "Streaming and Collision");
  *   - per-link boundaries compiled into the sweep through a flag field
@@ -72,7 +73,10 @@ typedef enum lbm_status {
 } lbm_status;
 
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
-enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2, LBM_CUMULANT = 3 };
+/* LBM_KBC: entropic KBC (Sec. III-C, Eq. entropic_linear_update and
+ * Eq. entropic_direct_omega_eq), the rate of the moments of order >= 3 chosen
+ * per cell and step from the linearised entropy condition */
+enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2, LBM_CUMULANT = 3, LBM_KBC = 4 };
 /* storage type of the population arrays; the collision computes in FP64 for
  * LBM_F64 and in FP32 for the others */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F32S = 3 };
@@ -89,7 +93,7 @@ enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_INLET = 2, LBM_OUTLET = 4 };
 
 typedef struct lbm_params {
   int32_t stencil;      /* LBM_D2Q9 | LBM_D3Q19 | LBM_D3Q27 */
-  int32_t collision;    /* LBM_SRT | LBM_TRT | LBM_MRT | LBM_CUMULANT */
+  int32_t collision;    /* LBM_SRT | LBM_TRT | LBM_MRT | LBM_CUMULANT | LBM_KBC */
   int32_t storage;      /* LBM_F64 | LBM_F32 | LBM_F16S | LBM_F32S */
   int32_t pattern;      /* LBM_PULL | LBM_AA */
   int32_t nx, ny, nz;   /* nz must be 1 for D2Q9; each >= 1 */
@@ -99,7 +103,10 @@ typedef struct lbm_params {
    *   TRT: omega[0] = omega_e (even moments), omega[1] = omega_o (odd).
    *   MRT: shear, bulk, 3rd-order, 4th-order, 5th-order, 6th-order rates
    *        (orders 5 and 6 exist for D3Q27 only); conserved moments use 0.
-   *   CUMULANT: shear, bulk, higher-order (orders >= 3). */
+   *   CUMULANT: shear, bulk, higher-order (orders >= 3).
+   *   KBC: omega[0] = shear rate omega_s, omega[1] = bulk rate (equal to
+   *        omega[0] gives the paper's two-rate form); the rate of orders >= 3
+   *        is not a parameter.  No body force, no Smagorinsky model. */
   double omega[6];
   int32_t trt_magic;    /* TRT: non-zero derives omega_o from omega_e and Lambda = magic */
   int32_t incompressible; /* non-zero: rho_0 = 1 in velocity terms (Sec. III-A) */
@@ -187,7 +194,8 @@ lbm_status lbm_set_pdfs(lbm_ctx* ctx, const void* src, int64_t t);
 lbm_status lbm_link_mask(lbm_ctx* ctx, uint32_t* mask);
 
 /* Replace the uniform body force (Guo scheme); takes effect for later
- * launches. */
+ * launches.  LBM_E_UNSUPPORTED for a non-zero force with cumulant or KBC
+ * collision. */
 lbm_status lbm_set_force(lbm_ctx* ctx, const double F[3]);
 
 /* One time step of the pull pattern from the population array src into dst
@@ -203,8 +211,9 @@ lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
  * device double[3] it points to.  lam_in, lam_out: device [q][N] arrays of FP64
  * when storage is LBM_F64, else FP32 (distinct).  P_prev: device population
  * array in the storage type.  Requires the pull pattern (LBM_E_STATE), SRT,
- * TRT or MRT (LBM_E_UNSUPPORTED for cumulant) and no OUTLET links
- * (LBM_E_UNSUPPORTED).  Non-fluid cells receive zero. */
+ * TRT or MRT without the Smagorinsky model (LBM_E_UNSUPPORTED for cumulant,
+ * KBC and Smagorinsky) and no OUTLET links (LBM_E_UNSUPPORTED).  Non-fluid
+ * cells receive zero. */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* P_prev, const void* lam_in, void* lam_out,
                             double* dLdF);
 

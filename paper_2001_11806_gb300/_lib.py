@@ -11,7 +11,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_ui
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbm.so")
 
 STENCILS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISIONS = {"srt": 0, "trt": 1, "mrt": 2, "cumulant": 3}
+COLLISIONS = {"srt": 0, "trt": 1, "mrt": 2, "cumulant": 3, "kbc": 4}
 STORAGES = {"f64": 0, "f32": 1, "f16s": 2, "f32s": 3}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "f32s": 4}
 PATTERNS = {"pull": 0, "aa": 1}

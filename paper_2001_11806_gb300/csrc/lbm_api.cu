@@ -114,7 +114,7 @@ bool rate_ok(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
 lbm_status validate(const lbm_params* p, std::string* msg) {
   if (!p) { *msg = "params is NULL"; return LBM_E_INVAL; }
   if (p->stencil < LBM_D2Q9 || p->stencil > LBM_D3Q27) { *msg = "unknown stencil"; return LBM_E_INVAL; }
-  if (p->collision < LBM_SRT || p->collision > LBM_CUMULANT) { *msg = "unknown collision"; return LBM_E_INVAL; }
+  if (p->collision < LBM_SRT || p->collision > LBM_KBC) { *msg = "unknown collision"; return LBM_E_INVAL; }
   if (p->storage < LBM_F64 || p->storage > LBM_F32S) { *msg = "unknown storage"; return LBM_E_INVAL; }
   if (p->pattern != LBM_PULL && p->pattern != LBM_AA) { *msg = "unknown pattern"; return LBM_E_INVAL; }
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) { *msg = "nx, ny, nz must be >= 1"; return LBM_E_INVAL; }
@@ -151,6 +151,14 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
       }
       if (p->incompressible) { *msg = "incompressible cumulant collision is not built"; return LBM_E_UNSUPPORTED; }
       break;
+    case LBM_KBC:
+      for (int i = 0; i < 2; ++i)
+        if (!rate_ok(p->omega[i])) { *msg = "KBC shear and bulk rates must be in (0, 2)"; return LBM_E_INVAL; }
+      if (p->force[0] != 0.0 || p->force[1] != 0.0 || p->force[2] != 0.0) {
+        *msg = "KBC collision with a body force is not built";
+        return LBM_E_UNSUPPORTED;
+      }
+      break;
   }
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(p->force[i]) || !std::isfinite(p->u_wall[i])) { *msg = "non-finite force or wall velocity"; return LBM_E_INVAL; }
@@ -159,7 +167,7 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
     *msg = "smagorinsky_cs must be >= 0";
     return LBM_E_INVAL;
   }
-  if (p->smagorinsky_cs > 0.0 && (p->collision == LBM_MRT || p->collision == LBM_CUMULANT)) {
+  if (p->smagorinsky_cs > 0.0 && p->collision != LBM_SRT && p->collision != LBM_TRT) {
     *msg = "the Smagorinsky model is built for SRT and TRT";
     return LBM_E_UNSUPPORTED;
   }
@@ -221,7 +229,7 @@ void fill_collide_params(lbm_ctx* c) {
   cp.smag_18cs2 = 18.0 * p.smagorinsky_cs * p.smagorinsky_cs;
   cp.smag_tau0 = 1.0 / om[0];
   cp.smag_lambda = p.magic;
-  c->kernel_op = p.collision;
+  c->kernel_op = p.collision == LBM_KBC ? OP_KBC : p.collision;
   if (cp.smag) c->kernel_op = p.collision == LBM_SRT ? OP_SRT_LES : OP_TRT_LES;
 }
 
@@ -437,7 +445,8 @@ lbm_status lbm_set_force(lbm_ctx* c, const double F[3]) {
   if (!c || !F) return LBM_E_INVAL;
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(F[i])) return LBM_E_INVAL;
-  if (c->p.collision == LBM_CUMULANT && (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0)) return LBM_E_UNSUPPORTED;
+  if ((c->p.collision == LBM_CUMULANT || c->p.collision == LBM_KBC) && (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0))
+    return LBM_E_UNSUPPORTED;
   for (int i = 0; i < 3; ++i) c->p.force[i] = F[i];
   fill_collide_params(c);
   return LBM_OK;
@@ -457,8 +466,8 @@ lbm_status adjoint_ok(lbm_ctx* c) {
     c->err = "the adjoint works on the two-array pull layout";
     return LBM_E_STATE;
   }
-  if (c->p.collision == LBM_CUMULANT) {
-    c->err = "the cumulant operator has no adjoint";
+  if (c->p.collision == LBM_CUMULANT || c->p.collision == LBM_KBC) {
+    c->err = "the cumulant and KBC operators have no adjoint";
     return LBM_E_UNSUPPORTED;
   }
   if (c->link_types & L_OUTLET) {

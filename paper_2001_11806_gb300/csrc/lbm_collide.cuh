@@ -21,8 +21,9 @@
 
 namespace lbm {
 
-// OP_SRT_LES / OP_TRT_LES: SRT / TRT with the Smagorinsky model compiled in
-enum Op : int { OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3, OP_SRT_LES = 4, OP_TRT_LES = 5 };
+// OP_SRT_LES / OP_TRT_LES: SRT / TRT with the Smagorinsky model compiled in;
+// OP_KBC: the entropic KBC operator
+enum Op : int { OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3, OP_SRT_LES = 4, OP_TRT_LES = 5, OP_KBC = 6 };
 
 // Runtime parameters of a sweep, passed by value to the kernel.
 struct CollideParams {
@@ -217,6 +218,126 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
     }
     v[q] = DH ? A + B : w + (A + B);
     v[q + 1] = DH ? A - B : w + (A - B);
+  }
+}
+
+// ---------------------------------------------------------------------- KBC
+// Entropic KBC (Sec. III-C, Eq. entropic_linear_update with a fixed bulk
+// rate): f - f^eq = Ds + Db + Dh with Ds the traceless and Db the trace part
+// of the second-order (Hermite) projection and Dh everything of order >= 3.
+// On D2Q9, D3Q19 and D3Q27 (sum w c_a^4 = 3 cs^4, sum w c_a^2 c_b^2 = cs^4)
+// the w-orthogonal projections are closed forms of Pi^neq:
+//   Ds_q = 4.5 w_q c_q . dev(Pi^neq) . c_q,
+//   Db_q = (4.5 / D) w_q (|c_q|^2 - D/3) tr(Pi^neq).
+// Both are even in c, so they live on the pair sums.  With
+// X = (1 - omega_s) Ds + (1 - omega_b) Db the post-collision state is
+//   f' = f^eq + X + (1 - omega_h) Dh,  1 - omega_h = -<X, Dh>_E / <Dh, Dh>_E
+// (the linearised entropy condition, Eq. entropic_direct_omega_eq), with
+// <a, b>_E = sum a b / f^eq.  For a pair (q, qbar) with f^eq = E +- O the two
+// reciprocals come from one: 1/(E+O) + 1/(E-O) = 2E/(E^2-O^2) and
+// 1/(E+O) - 1/(E-O) = -2O/(E^2-O^2).  Works on h = f - w; no body force.
+template <class L, class T>
+__device__ __forceinline__ T kbc_quad(int q, const T (&pd)[6]) {
+  // c . P . c for the symmetric P stored as (xx, yy, zz, xy, xz, yz)
+  const int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
+  T r = T(0);
+  if (cx) r += pd[0];
+  if (cy) r += pd[1];
+  if (cz) r += pd[2];
+  if (cx && cy) r += cx * cy > 0 ? T(2) * pd[3] : T(-2) * pd[3];
+  if (cx && cz) r += cx * cz > 0 ? T(2) * pd[4] : T(-2) * pd[4];
+  if (cy && cz) r += cy * cz > 0 ? T(2) * pd[5] : T(-2) * pd[5];
+  return r;
+}
+
+template <class L, class T>
+__device__ __forceinline__ void collide_kbc(T (&v)[L::Q], const CollideParams& p) {
+  constexpr int NP = (L::Q - 1) / 2;
+  constexpr int D = L::D;
+  T e[NP], o[NP];
+  const T h0 = v[0];
+  T drho = h0;
+  T jx = T(0), jy = T(0), jz = T(0);
+  bool ix = false, iy = false, iz = false;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    e[k] = v[q] + v[q + 1];
+    o[k] = v[q] - v[q + 1];
+    drho += e[k];
+    acc_signed(jx, ix, L::cx(q), o[k]);
+    acc_signed(jy, iy, L::cy(q), o[k]);
+    acc_signed(jz, iz, L::cz(q), o[k]);
+  }
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, D == 3 ? jz * inv : T(0)};
+  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T base = drho - T(1.5) * rho0 * usq;
+  const T k45 = T(4.5) * rho0;
+  const T m3 = T(3) * rho0;
+  // pair sums and differences of f - f^eq (halved): e_k, o_k; Pi^neq from e
+  T pn[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    const T g = e[k] - T(2) * w * fma(k45, cu * cu, base);
+    const int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
+    if (cx) pn[0] += g;
+    if (cy) pn[1] += g;
+    if (cz) pn[2] += g;
+    if (cx && cy) pn[3] += cx * cy > 0 ? g : -g;
+    if (cx && cz) pn[4] += cx * cz > 0 ? g : -g;
+    if (cy && cz) pn[5] += cy * cz > 0 ? g : -g;
+    e[k] = T(0.5) * g;
+    o[k] = T(0.5) * o[k] - m3 * w * cu;
+  }
+  const T tr = pn[0] + pn[1] + pn[2];
+  const T mean = tr * T(1.0 / D);
+  pn[0] -= mean; pn[1] -= mean; pn[2] -= mean;
+  if (D == 2) pn[2] = T(0);
+  const T cs1 = T(1) - rate<T>(p, 0), cb1 = T(1) - rate<T>(p, 1);
+  const T kb = T(4.5 / D) * tr;
+  // X_q / w_q = (1 - omega_s) 4.5 c.dev.c + (1 - omega_b) (4.5/D)(|c|^2 - D/3) tr
+  // e_k <- Dh even part = e_k - (Ds + Db)_q; rest: Ds_0 = 0, Db_0 = -1.5 w_0 tr
+  const T w0 = T(L::w(0));
+  const T X0 = cb1 * (T(-1.5) * w0 * tr);
+  const T dh0 = (h0 - w0 * base) + T(1.5) * w0 * tr;
+  const T feq0 = w0 * (T(1) + base);
+  T num = X0 * dh0 / feq0;
+  T den = dh0 * dh0 / feq0;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    const int c2 = L::cx(q) * L::cx(q) + L::cy(q) * L::cy(q) + L::cz(q) * L::cz(q);
+    const T ds = T(4.5) * w * kbc_quad<L, T>(q, pn);
+    const T db = w * kb * T(c2 - D / 3.0);
+    const T X = cs1 * ds + cb1 * db;
+    e[k] -= ds + db;
+    const T E = w * (T(1) + fma(k45, cu * cu, base));
+    const T O = m3 * w * cu;
+    const T iD = T(1) / (E * E - O * O);
+    const T Pp = T(2) * E * iD, Pm = T(-2) * O * iD;
+    num = fma(X, fma(e[k], Pp, o[k] * Pm), num);
+    den = fma(fma(e[k], e[k], o[k] * o[k]), Pp, fma(T(2) * e[k] * o[k], Pm, den));
+  }
+  const T mh = den > T(1e-30) ? -num / den : T(0);  // 1 - omega_h
+  v[0] = fma(mh, dh0, w0 * base + X0);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    const int c2 = L::cx(q) * L::cx(q) + L::cy(q) * L::cy(q) + L::cz(q) * L::cz(q);
+    const T X = cs1 * (T(4.5) * w * kbc_quad<L, T>(q, pn)) + cb1 * (w * kb * T(c2 - D / 3.0));
+    const T A = fma(mh, e[k], fma(w, fma(k45, cu * cu, base), X));
+    const T B = fma(mh, o[k], m3 * w * cu);
+    v[q] = A + B;
+    v[q + 1] = A - B;
   }
 }
 

@@ -211,6 +211,11 @@ __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, st
   collide_mrt<L, T>(v, p);
 }
 template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_KBC>) {
+  static_assert(DH, "KBC works on shifted populations");
+  collide_kbc<L, T>(v, p);
+}
+template <class L, class T, bool DH>
 __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_CUM>) {
   static_assert(DH, "the cumulant operator works on shifted populations");
   if constexpr (L::Q == 27) collide_cumulant<T>(v, p);

@@ -17,6 +17,7 @@ struct Ops {
       case OP_MRT: return launch_sweep_op<L, ST, OP_MRT>(kind, bnd, a, s);
       case OP_SRT_LES: return launch_sweep_op<L, ST, OP_SRT_LES>(kind, bnd, a, s);
       case OP_TRT_LES: return launch_sweep_op<L, ST, OP_TRT_LES>(kind, bnd, a, s);
+      case OP_KBC: return launch_sweep_op<L, ST, OP_KBC>(kind, bnd, a, s);
       case OP_CUM:
         if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s);
         return cudaErrorInvalidValue;

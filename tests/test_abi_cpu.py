@@ -44,9 +44,9 @@ def _params(**kw):
         if k == "omega":
             for i, x in enumerate(v):
                 p.omega[i] = x
-        elif k == "periodic":
+        elif k in ("periodic", "force"):
             for i, x in enumerate(v):
-                p.periodic[i] = x
+                getattr(p, k)[i] = x
         else:
             setattr(p, k, v)
     return p
@@ -73,6 +73,9 @@ def test_query_sizes(L):
     (dict(stencil=0, nz=2), 1), (dict(omega=[2.5]), 1), (dict(omega=[0.0]), 1), (dict(ny=70000), 1),
     (dict(collision=3, stencil=1, omega=[1.5, 1, 1]), 2), (dict(collision=3, stencil=0, nz=1, omega=[1.5, 1, 1]), 2),
     (dict(rho_outlet=-1.0), 1), (dict(collision=1, trt_magic=1, magic=-1.0), 1),
+    (dict(collision=4, omega=[1.9, 0.0]), 1), (dict(collision=4, omega=[1.9, 1.0], force=(1e-4, 0.0, 0.0)), 2),
+    (dict(collision=4, omega=[1.9, 1.0], smagorinsky_cs=0.1), 2), (dict(collision=2, smagorinsky_cs=0.1), 2),
+    (dict(collision=5), 1),
 ])
 def test_invalid_parameters(L, kw, status):
     s, _, _ = _query(_params(**kw))

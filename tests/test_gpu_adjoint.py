@@ -157,7 +157,8 @@ def test_autograd_function_and_unsupported_cases():
     # the adjoint refuses what it does not differentiate
     fl = np.zeros((4, 5, 6), np.uint8)
     fl[:, :, -1] = olbm.OUTLET
-    for kw, status in [(dict(collision="trt", pattern="aa"), 8), (dict(collision="trt", flags=fl), 2)]:
+    for kw, status in [(dict(collision="trt", pattern="aa"), 8), (dict(collision="trt", flags=fl), 2),
+                       (dict(collision="kbc"), 2)]:
         sim = Sim("D3Q19", kw["collision"], "f64", kw.get("pattern", "pull"), (6, 5, 4), omega=[1.2, 1.1],
                   flags=kw.get("flags"), periodic=(False, True, True))
         buf = torch.zeros((19, sim.N), dtype=torch.float64, device=sim.device)

@@ -20,7 +20,8 @@ from paper_2001_11806_gb300.sim import Sim
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5, "f32s": 1e-5, "f16s": 5e-3}
-OMEGAS = {"srt": [1.37], "trt": [1.8, 8 / 31], "mrt": [1.7, 1.1, 0.9, 1.3, 1.2, 1.05], "cumulant": [1.95, 1.0, 1.0]}
+OMEGAS = {"srt": [1.37], "trt": [1.8, 8 / 31], "mrt": [1.7, 1.1, 0.9, 1.3, 1.2, 1.05], "cumulant": [1.95, 1.0, 1.0],
+          "kbc": [1.9, 1.3]}
 
 
 def _shape(stencil, big=True):
@@ -83,7 +84,7 @@ def _errs(r):
     return ef, er, eu
 
 
-COMBOS = [(s, c) for s in ["D2Q9", "D3Q19", "D3Q27"] for c in ["srt", "trt", "mrt"]] + [("D3Q27", "cumulant")]
+COMBOS = [(s, c) for s in ["D2Q9", "D3Q19", "D3Q27"] for c in ["srt", "trt", "mrt", "kbc"]] + [("D3Q27", "cumulant")]
 
 
 @pytest.mark.parametrize("stencil,collision", COMBOS)
@@ -114,7 +115,7 @@ def test_channel_parity(stencil, collision, storage, pattern, steps):
     assert np.array_equal(mask, r["ref"].link_mask().reshape(-1))
 
 
-@pytest.mark.parametrize("stencil,collision", [c for c in COMBOS if c[1] != "cumulant"])
+@pytest.mark.parametrize("stencil,collision", [c for c in COMBOS if c[1] not in ("cumulant", "kbc")])
 @pytest.mark.parametrize("pattern", ["pull", "aa"])
 @pytest.mark.parametrize("incompressible", [False, True])
 def test_force_parity(stencil, collision, pattern, incompressible):
@@ -263,7 +264,7 @@ def test_poiseuille_exact_on_gpu():
 
 
 @pytest.mark.parametrize("stencil,collision", [("D2Q9", "trt"), ("D3Q19", "trt"), ("D3Q19", "mrt"),
-                                               ("D3Q27", "srt"), ("D3Q27", "cumulant")])
+                                               ("D3Q27", "srt"), ("D3Q27", "cumulant"), ("D3Q19", "kbc")])
 @pytest.mark.parametrize("pattern", ["pull", "aa"])
 @pytest.mark.parametrize("nx", [534, 151])
 def test_f16_two_cell_kernel_parity(stencil, collision, pattern, nx):
@@ -303,3 +304,36 @@ def test_smagorinsky_parity(stencil, collision, magic, storage, pattern):
     fr = ref.populations().reshape(lat.q, -1)[:, fluid]
     err = np.linalg.norm(fg - fr) / np.linalg.norm(fr - lat.w[:, None])
     assert err < TOL[storage], err
+
+
+@pytest.mark.parametrize("stencil", ["D2Q9", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_kbc_incompressible_and_two_rate_form(stencil, storage):
+    """KBC with the incompressible equilibrium, and with omega_b = omega_s
+    (the paper's two-rate form), walls and a moving inlet."""
+    lat = olat.get(stencil)
+    shape = _shape(stencil)
+    fl = _flags(shape)
+    for om, inc in (([1.95, 1.95], False), ([1.6, 0.7], True)):
+        sim = Sim(stencil, "kbc", storage, "aa", shape, periodic=(False, False, True), omega=om,
+                  incompressible=inc, u_wall=(0.05, 0.0, 0.0), flags=fl)
+        P = inputs.random_pdfs(lat.w, shape[::-1], amp=0.05, seed=31)
+        sim.set_state(P.reshape(lat.q, -1))
+        sim.step(5)
+        ref = olbm.Sim(oco.Method(lat, "kbc", om, incompressible=inc), shape, periodic=(False, False, True), flags=fl,
+                       u_wall=(0.05, 0.0, 0.0))
+        ref.P = P.copy()
+        ref.step(5)
+        fluid = fl.reshape(-1) == 0
+        fg = sim.populations().cpu().numpy()[:, fluid]
+        fr = ref.populations().reshape(lat.q, -1)[:, fluid]
+        err = np.linalg.norm(fg - fr) / np.linalg.norm(fr - lat.w[:, None])
+        assert err < TOL[storage], (om, inc, err)
+
+
+def test_kbc_unsupported_combinations():
+    from paper_2001_11806_gb300 import LbmError
+    with pytest.raises(LbmError):
+        Sim("D3Q19", "kbc", "f32", "pull", (8, 8, 8), omega=[1.9, 1.0], force=(1e-4, 0.0, 0.0))
+    with pytest.raises(LbmError):
+        Sim("D3Q19", "kbc", "f32", "pull", (8, 8, 8), omega=[1.9, 1.0], smagorinsky_cs=0.1)

@@ -196,8 +196,26 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
     const size_t off = q < c->q ? size_t(q) * size_t(c->N) * c->elem : 0;
     a.srcq[q] = src ? static_cast<const char*>(src) + off : nullptr;
     a.dstq[q] = dst ? static_cast<char*>(dst) + off : nullptr;
+    a.srci[q] = nullptr;
+    a.dsti[q] = nullptr;
   }
   return a;
+}
+
+// Shifted stream bases of the fast path of periodic pull / AA odd sweeps
+// (SweepArgs::srci, dsti); unused by the other kinds.
+void set_interior(SweepArgs& a, const lbm_ctx* c, int kind) {
+  if (kind == K_AA_EVEN) return;
+  int32_t cv[27 * 3];
+  lbm_stencil_info(c->p.stencil, nullptr, nullptr, cv, nullptr);
+  const long long nx = c->p.nx, nxy = (long long)c->p.nx * c->p.ny;
+  for (int q = 0; q < c->q; ++q) {
+    const long long off = (cv[3 * q] + nx * cv[3 * q + 1] + nxy * cv[3 * q + 2]) * (long long)c->elem;
+    const int qbar = q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1);
+    const int qs = kind == K_AA_ODD ? qbar : q;
+    a.srci[q] = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(a.srcq[qs]) - off);
+    a.dsti[q] = kind == K_AA_ODD ? reinterpret_cast<char*>(reinterpret_cast<uintptr_t>(a.dstq[q]) + off) : nullptr;
+  }
 }
 
 int current_view(const lbm_ctx* c) {
@@ -362,11 +380,14 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     cudaError_t e;
     if (c->p.pattern == LBM_PULL) {
       SweepArgs a = make_args(c, c->buf[c->cur], c->buf[1 - c->cur]);
+      set_interior(a, c, K_PULL);
       e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
       if (e == cudaSuccess) c->cur = 1 - c->cur;
     } else {
       SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
-      e = c->ops.sweep(c->kernel_op, (c->t & 1) ? K_AA_ODD : K_AA_EVEN, c->has_mask, a, c->stream);
+      const int kind = (c->t & 1) ? K_AA_ODD : K_AA_EVEN;
+      set_interior(a, c, kind);
+      e = c->ops.sweep(c->kernel_op, kind, c->has_mask, a, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "step");
     ++c->t;
@@ -456,6 +477,7 @@ lbm_status lbm_step_pull(lbm_ctx* c, const void* src, void* dst) {
   if (!c || !src || !dst || src == dst) return LBM_E_INVAL;
   if (c->p.pattern != LBM_PULL) return LBM_E_STATE;
   SweepArgs a = make_args(c, src, dst);
+  set_interior(a, c, K_PULL);
   cudaError_t e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "step_pull");
 }

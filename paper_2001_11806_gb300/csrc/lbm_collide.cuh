@@ -233,9 +233,21 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
 // X = (1 - omega_s) Ds + (1 - omega_b) Db the post-collision state is
 //   f' = f^eq + X + (1 - omega_h) Dh,  1 - omega_h = -<X, Dh>_E / <Dh, Dh>_E
 // (the linearised entropy condition, Eq. entropic_direct_omega_eq), with
-// <a, b>_E = sum a b / f^eq.  For a pair (q, qbar) with f^eq = E +- O the two
-// reciprocals come from one: 1/(E+O) + 1/(E-O) = 2E/(E^2-O^2) and
-// 1/(E+O) - 1/(E-O) = -2O/(E^2-O^2).  Works on h = f - w; no body force.
+// <a, b>_E = sum a b / f^eq.  Works on h = f - w; no body force.  Passes over
+// the pairs: moments; Pi^neq; projections, the two scalar products and
+// h^eq + X; then the (1 - omega_h) Dh term.
+//
+// 1/x for the entropic weights: the PTX approximate reciprocal in FP32
+// (rcp.approx.ftz.f32; the arguments are values of f^eq, far from the
+// subnormal range), an IEEE division in FP64
+template <class T> __device__ __forceinline__ T kbc_rcp(T x);
+template <> __device__ __forceinline__ float kbc_rcp<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+template <> __device__ __forceinline__ double kbc_rcp<double>(double x) { return 1.0 / x; }
+
 template <class L, class T>
 __device__ __forceinline__ T kbc_quad(int q, const T (&pd)[6]) {
   // c . P . c for the symmetric P stored as (xx, yy, zz, xy, xz, yz)
@@ -306,8 +318,9 @@ __device__ __forceinline__ void collide_kbc(T (&v)[L::Q], const CollideParams& p
   const T X0 = cb1 * (T(-1.5) * w0 * tr);
   const T dh0 = (h0 - w0 * base) + T(1.5) * w0 * tr;
   const T feq0 = w0 * (T(1) + base);
-  T num = X0 * dh0 / feq0;
-  T den = dh0 * dh0 / feq0;
+  const T i0 = kbc_rcp(feq0);
+  T num = X0 * dh0 * i0;
+  T den = dh0 * dh0 * i0;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = 2 * k + 1;
@@ -318,26 +331,27 @@ __device__ __forceinline__ void collide_kbc(T (&v)[L::Q], const CollideParams& p
     const T db = w * kb * T(c2 - D / 3.0);
     const T X = cs1 * ds + cb1 * db;
     e[k] -= ds + db;
-    const T E = w * (T(1) + fma(k45, cu * cu, base));
-    const T O = m3 * w * cu;
-    const T iD = T(1) / (E * E - O * O);
-    const T Pp = T(2) * E * iD, Pm = T(-2) * O * iD;
-    num = fma(X, fma(e[k], Pp, o[k] * Pm), num);
-    den = fma(fma(e[k], e[k], o[k] * o[k]), Pp, fma(T(2) * e[k] * o[k], Pm, den));
+    const T a = fma(k45, cu * cu, base);
+    const T E = fma(w, a, w);  // f^eq_q = E + O, f^eq_qbar = E - O
+    const T O = (m3 * w) * cu;
+    const T hp = e[k] + o[k], hm = e[k] - o[k];  // Dh_q, Dh_qbar
+    const T tp = hp * kbc_rcp(E + O), tm = hm * kbc_rcp(E - O);
+    num = fma(X, tp + tm, num);
+    den = fma(tp, hp, fma(tm, hm, den));
+    // h^eq + X now, (1 - omega_h) Dh once omega_h is known
+    const T A0 = fma(w, a, X);
+    v[q] = A0 + O;
+    v[q + 1] = A0 - O;
+    e[k] = hp;
+    o[k] = hm;
   }
   const T mh = den > T(1e-30) ? -num / den : T(0);  // 1 - omega_h
   v[0] = fma(mh, dh0, w0 * base + X0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = 2 * k + 1;
-    const T w = T(L::w(q));
-    const T cu = cdot<L, T>(q, u);
-    const int c2 = L::cx(q) * L::cx(q) + L::cy(q) * L::cy(q) + L::cz(q) * L::cz(q);
-    const T X = cs1 * (T(4.5) * w * kbc_quad<L, T>(q, pn)) + cb1 * (w * kb * T(c2 - D / 3.0));
-    const T A = fma(mh, e[k], fma(w, fma(k45, cu * cu, base), X));
-    const T B = fma(mh, o[k], m3 * w * cu);
-    v[q] = A + B;
-    v[q + 1] = A - B;
+    v[q] = fma(mh, e[k], v[q]);
+    v[q + 1] = fma(mh, o[k], v[q + 1]);
   }
 }
 

@@ -48,6 +48,14 @@ struct SweepArgs {
   // lives in the kernel's constant bank
   const char* srcq[27];
   char* dstq[27];
+  // K_PULL and K_AA_ODD sweeps of fully periodic domains: the stream each
+  // direction q reads from (AA odd: slot qbar), shifted by the neighbour
+  // offset -(c_qx + nx c_qy + nx ny c_qz) cells, and (AA odd) the stream it
+  // writes to, shifted by +(...).  A cell whose y and z neighbours do not
+  // wrap then reaches every neighbour with one cell offset (plus a per-thread
+  // x wrap), as the AA even sweep does.
+  const char* srci[27];
+  char* dsti[27];
 };
 
 constexpr int kBlockX = 128;
@@ -73,6 +81,15 @@ __device__ __forceinline__ Nbr make_nbr(const Geom& g, int x, int y, int z) {
   n.zo[1] = z * sz;
   n.zo[2] = (z == g.nz - 1 ? 0 : z + 1) * sz;
   return n;
+}
+
+// True when the y and z neighbours of row (y, z) lie inside the box without
+// wrapping (1 <= y <= ny - 2 and, in 3-D, 1 <= z <= nz - 2).
+template <class L>
+__device__ __forceinline__ bool row_inner(const Geom& g, int y, int z) {
+  const bool iy = unsigned(y - 1) < unsigned(g.ny - 2);
+  if constexpr (L::D == 2) return iy;
+  else return iy && unsigned(z - 1) < unsigned(g.nz - 2);
 }
 
 // Boundary type of the link whose source cell is (sx, sy, sz) (may lie one
@@ -244,10 +261,22 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
   }
   const Nbr nb = make_nbr(a.g, x, y, z);
   T v[L::Q];
+  // periodic sweeps of rows away from the y and z faces (uniform per block)
+  bool fast = false;
+  if constexpr (!BND && KIND != K_AA_EVEN) fast = row_inner<L>(a.g, y, z);
 
   if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) v[q] = D::load(reinterpret_cast<const S*>(a.srcq[q])[cell], L::w(q));
+  } else if (fast) {
+    // x - c_q with the x wrap: c_x = +1 reads x - 1 (wraps at x = 0), c_x = -1 reads x + 1
+    const int im = cell + (x == 0 ? a.g.nx : 0);
+    const int ip = cell - (x == a.g.nx - 1 ? a.g.nx : 0);
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      const int idx = L::cx(q) > 0 ? im : (L::cx(q) < 0 ? ip : cell);
+      v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[idx], L::w(q));
+    }
   } else {
     // pull:   fluid source -> P_q(x - c_q) = src[q][x - c_q];  boundary -> P_qbar(x) = src[qbar][x]
     // AA odd: fluid source -> A[qbar][x - c_q];                 boundary -> A[q][x]
@@ -307,15 +336,28 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
       // offsets are not held in registers across the collision.
       int tx;
       asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
-      const Nbr nbs = make_nbr(a.g, blockIdx.x * blockDim.x + tx, y, z);
+      const int xs = blockIdx.x * blockDim.x + tx;
+      if (fast) {
+        // x + c_q with the x wrap: c_x = +1 writes x + 1 (wraps at nx - 1), c_x = -1 writes x - 1
+        const int cs = xs + a.g.nx * (y + a.g.ny * z);
+        const int ip = cs - (xs == a.g.nx - 1 ? a.g.nx : 0);
+        const int im = cs + (xs == 0 ? a.g.nx : 0);
 #pragma unroll
-      for (int q = 0; q < L::Q; ++q) {
-        // AA odd: fluid destination -> A[q][x + c_q]; boundary -> A[p][x]
-        const int p = opp(q);
-        const bool b = BND && ((mask >> p) & 1u);
-        const int qd = b ? p : q;
-        const int idx = b ? cell : nbs.at(L::cx(q), L::cy(q), L::cz(q));
-        reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+        for (int q = 0; q < L::Q; ++q) {
+          const int idx = L::cx(q) > 0 ? ip : (L::cx(q) < 0 ? im : cs);
+          reinterpret_cast<S*>(a.dsti[q])[idx] = D::store(v[q], L::w(q));
+        }
+      } else {
+        const Nbr nbs = make_nbr(a.g, xs, y, z);
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) {
+          // AA odd: fluid destination -> A[q][x + c_q]; boundary -> A[p][x]
+          const int p = opp(q);
+          const bool b = BND && ((mask >> p) & 1u);
+          const int qd = b ? p : q;
+          const int idx = b ? cell : nbs.at(L::cx(q), L::cy(q), L::cz(q));
+          reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+        }
       }
     }
   }

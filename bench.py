@@ -234,6 +234,8 @@ def run_variants(device, peak):
                                                   shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
         ("D3Q19 TRT FP16-shifted 256^3 AA", dict(stencil="D3Q19", collision="trt", storage="f16s", pattern="aa",
                                                  shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
+        ("D3Q19 TRT FP32 256^3 esoteric twist", dict(stencil="D3Q19", collision="trt", storage="f32", pattern="eso",
+                                                     shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
         ("D3Q19 SRT + Smagorinsky (C_S 0.17) FP32 256^3 AA",
          dict(stencil="D3Q19", collision="srt", storage="f32", pattern="aa", shape=(256,) * 3, omega=[1.95],
               smagorinsky_cs=0.17), "tgv", 300),

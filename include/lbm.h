@@ -13,7 +13,8 @@
  *     cumulant collision for D3Q27 (Sec. III-B, Eq.
  *     cumulant_generating_function), the Smagorinsky model for SRT/TRT and
  *     the entropic KBC operator (Sec. III-C);
- *   - two-array stream-pull-collide and single-array AA update patterns
+ *   - two-array stream-pull-collide and single-array AA and esoteric-twist
+ *     update patterns
  *     (Sec. IV-B "Streaming and Collision");
  *   - per-link boundaries compiled into the sweep through a flag field
  *     (Sec. IV-B "Boundary Conditions"): halfway bounce-back, velocity
@@ -80,7 +81,19 @@ enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2, LBM_CUMULANT = 3, LBM_KBC = 4 };
 /* storage type of the population arrays; the collision computes in FP64 for
  * LBM_F64 and in FP32 for the others */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F32S = 3 };
-enum { LBM_PULL = 0, LBM_AA = 1 };
+/* update pattern (Sec. IV-B "Streaming and Collision"):
+ *   LBM_PULL: two arrays, stream-pull-collide, swapped every step;
+ *   LBM_AA: one array; even steps read and write a cell's own slots, odd
+ *     steps read and write its neighbours';
+ *   LBM_ESOTWIST: one array; every step reads and writes the slots at the
+ *     cell and at its positive neighbours x + max(c_q, 0): f_q(x) is read from
+ *     location x + max(-c_q, 0) (slot q after an even number of steps, slot
+ *     qbar after an odd number) and P_q(x) written to x + max(c_q, 0) (slot
+ *     qbar in even steps, q in odd steps; a boundary link (x, qbar) takes the
+ *     other slot).  Locations wrap on every axis, so along a non-periodic
+ *     axis the last layer (index n - 1) must be non-fluid (a wall, inlet or
+ *     outlet layer); lbm_create returns LBM_E_UNSUPPORTED otherwise. */
+enum { LBM_PULL = 0, LBM_AA = 1, LBM_ESOTWIST = 2 };
 /* uint8 flag per cell; 0 = fluid.  A boundary link (x, q) takes its type from
  * the flag of its source cell x - c_q with precedence NOSLIP > INLET > OUTLET
  * (a non-zero flag with none of these bits counts as NOSLIP).  Sources outside
@@ -95,7 +108,7 @@ typedef struct lbm_params {
   int32_t stencil;      /* LBM_D2Q9 | LBM_D3Q19 | LBM_D3Q27 */
   int32_t collision;    /* LBM_SRT | LBM_TRT | LBM_MRT | LBM_CUMULANT | LBM_KBC */
   int32_t storage;      /* LBM_F64 | LBM_F32 | LBM_F16S | LBM_F32S */
-  int32_t pattern;      /* LBM_PULL | LBM_AA */
+  int32_t pattern;      /* LBM_PULL | LBM_AA | LBM_ESOTWIST */
   int32_t nx, ny, nz;   /* nz must be 1 for D2Q9; each >= 1 */
   int32_t periodic[3];  /* non-zero = periodic along x, y, z */
   /* relaxation rates, each in (0, 2):
@@ -139,7 +152,7 @@ lbm_status lbm_query_sizes(const lbm_params* p, size_t* pdf_bytes, size_t* aux_b
 
 /* Create a context over caller-owned device buffers.
  *   pdf, pdf2: population arrays of pdf_bytes each; pdf2 must be non-NULL for
- *     LBM_PULL and is ignored (may be NULL) for LBM_AA.
+ *     LBM_PULL and is ignored (may be NULL) for LBM_AA and LBM_ESOTWIST.
  *   aux: auxiliary device buffer of aux_bytes.
  *   flags: device uint8[N] flag field or NULL (all fluid).  It is read at
  *     creation (to build the link mask) and on boundary links during steps.
@@ -164,7 +177,8 @@ lbm_status lbm_set_state(lbm_ctx* ctx, const double* P);
 /* Advance n >= 0 time steps (asynchronous). */
 lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
 
-/* Number of steps since the last initialisation (AA parity = t mod 2). */
+/* Number of steps since the last initialisation (AA and esoteric-twist parity
+ * = t mod 2). */
 lbm_status lbm_get_time(const lbm_ctx* ctx, int64_t* t);
 
 /* Populations f of the current time (streamed, pre-collision, unshifted) as
@@ -183,7 +197,7 @@ lbm_status lbm_reduce(lbm_ctx* ctx, double out[5]);
 
 /* Raw copy of the native population storage (pdf_bytes, device to device),
  * for checkpoint/restore.  lbm_set_pdfs also sets the step counter to t so
- * that the AA parity matches the saved data. */
+ * that the AA or esoteric-twist parity matches the saved data. */
 lbm_status lbm_get_pdfs(lbm_ctx* ctx, void* dst);
 lbm_status lbm_set_pdfs(lbm_ctx* ctx, const void* src, int64_t t);
 
@@ -242,7 +256,7 @@ lbm_status lbm_eq_vjp(lbm_ctx* ctx, const double* rho0, const double* u0, const 
  *   pdf:    device population array in the native layout, as lbm_get_pdfs
  *           returns it (for LBM_PULL the array holding the current state);
  *   flags:  device uint8[N] flag field or NULL (all fluid);
- *   t:      the step count of that state (selects the AA parity);
+ *   t:      the step count of that state (selects the AA / esoteric-twist parity);
  *   out:    device double[5]; receives the same five sums as lbm_reduce;
  *   stream: cudaStream_t (NULL = legacy default stream); the call enqueues work
  *           and returns without synchronising.

@@ -14,7 +14,7 @@ STENCILS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
 COLLISIONS = {"srt": 0, "trt": 1, "mrt": 2, "cumulant": 3, "kbc": 4}
 STORAGES = {"f64": 0, "f32": 1, "f16s": 2, "f32s": 3}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "f32s": 4}
-PATTERNS = {"pull": 0, "aa": 1}
+PATTERNS = {"pull": 0, "aa": 1, "eso": 2}
 STATUS = ["LBM_OK", "LBM_E_INVAL", "LBM_E_UNSUPPORTED", "LBM_E_CUDA", "LBM_E_NOMEM", "LBM_E_BUFSIZE",
           "LBM_E_NONFINITE", "LBM_E_BOUNDS", "LBM_E_STATE"]
 FLUID, NOSLIP, INLET, OUTLET = 0, 1, 2, 4

@@ -116,7 +116,10 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
   if (p->stencil < LBM_D2Q9 || p->stencil > LBM_D3Q27) { *msg = "unknown stencil"; return LBM_E_INVAL; }
   if (p->collision < LBM_SRT || p->collision > LBM_KBC) { *msg = "unknown collision"; return LBM_E_INVAL; }
   if (p->storage < LBM_F64 || p->storage > LBM_F32S) { *msg = "unknown storage"; return LBM_E_INVAL; }
-  if (p->pattern != LBM_PULL && p->pattern != LBM_AA) { *msg = "unknown pattern"; return LBM_E_INVAL; }
+  if (p->pattern != LBM_PULL && p->pattern != LBM_AA && p->pattern != LBM_ESOTWIST) {
+    *msg = "unknown pattern";
+    return LBM_E_INVAL;
+  }
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) { *msg = "nx, ny, nz must be >= 1"; return LBM_E_INVAL; }
   if (p->stencil == LBM_D2Q9 && p->nz != 1) { *msg = "D2Q9 needs nz == 1"; return LBM_E_INVAL; }
   if (p->ny > 65535 || p->nz > 65535) { *msg = "ny and nz must be <= 65535"; return LBM_E_INVAL; }
@@ -204,22 +207,38 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
 
 // Shifted stream bases of the fast path of periodic pull / AA odd sweeps
 // (SweepArgs::srci, dsti); unused by the other kinds.
+// Esoteric twist: the read base of direction q is its slot (q even, qbar
+// odd) shifted to location x + max(-c_q, 0), the write base its slot (qbar
+// even, q odd) shifted to x + max(c_q, 0).
 void set_interior(SweepArgs& a, const lbm_ctx* c, int kind) {
   if (kind == K_AA_EVEN) return;
   int32_t cv[27 * 3];
   lbm_stencil_info(c->p.stencil, nullptr, nullptr, cv, nullptr);
   const long long nx = c->p.nx, nxy = (long long)c->p.nx * c->p.ny;
+  const long long el = (long long)c->elem;
+  auto shift = [](const void* p, long long bytes) {
+    return reinterpret_cast<char*>(reinterpret_cast<uintptr_t>(p) + bytes);
+  };
   for (int q = 0; q < c->q; ++q) {
-    const long long off = (cv[3 * q] + nx * cv[3 * q + 1] + nxy * cv[3 * q + 2]) * (long long)c->elem;
+    const int cx = cv[3 * q], cy = cv[3 * q + 1], cz = cv[3 * q + 2];
+    const long long off = (cx + nx * cy + nxy * cz) * el;
     const int qbar = q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1);
+    if (kind == K_ESO_EVEN || kind == K_ESO_ODD) {
+      const long long rd = (eso_rd(cx) + nx * eso_rd(cy) + nxy * eso_rd(cz)) * el;
+      const long long wr = (eso_wr(cx) + nx * eso_wr(cy) + nxy * eso_wr(cz)) * el;
+      a.srci[q] = shift(a.srcq[kind == K_ESO_EVEN ? q : qbar], rd);
+      a.dsti[q] = shift(a.dstq[kind == K_ESO_EVEN ? qbar : q], wr);
+      continue;
+    }
     const int qs = kind == K_AA_ODD ? qbar : q;
-    a.srci[q] = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(a.srcq[qs]) - off);
-    a.dsti[q] = kind == K_AA_ODD ? reinterpret_cast<char*>(reinterpret_cast<uintptr_t>(a.dstq[q]) + off) : nullptr;
+    a.srci[q] = shift(a.srcq[qs], -off);
+    a.dsti[q] = kind == K_AA_ODD ? shift(a.dstq[q], off) : nullptr;
   }
 }
 
 int current_view(const lbm_ctx* c) {
   if (c->p.pattern == LBM_PULL) return V_PULL;
+  if (c->p.pattern == LBM_ESOTWIST) return (c->t & 1) ? V_ESO_ODD : V_ESO_EVEN;
   return (c->t & 1) ? V_AA_INVERTED : V_AA_NATURAL;
 }
 
@@ -343,6 +362,10 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
       delete c;
       return LBM_E_CUDA;
     }
+    if (p->pattern == LBM_ESOTWIST && (c->link_types & TYPES_FLUID_LAST_LAYER)) {
+      delete c;
+      return LBM_E_UNSUPPORTED;
+    }
   }
   *out = c;
   return LBM_OK;
@@ -358,7 +381,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) 
   if (!c || !rho || !u) return LBM_E_INVAL;
   c->cur = 0;
   SweepArgs a = make_args(c, nullptr, c->buf[0]);
-  cudaError_t e = c->ops.set_state(c->p.pattern == LBM_AA, 1, a, nullptr, rho, u, c->stream);
+  cudaError_t e = c->ops.set_state(c->p.pattern, 1, a, nullptr, rho, u, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init_equilibrium");
   c->t = 0;
   return LBM_OK;
@@ -368,7 +391,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* P) {
   if (!c || !P) return LBM_E_INVAL;
   c->cur = 0;
   SweepArgs a = make_args(c, nullptr, c->buf[0]);
-  cudaError_t e = c->ops.set_state(c->p.pattern == LBM_AA, 0, a, P, nullptr, nullptr, c->stream);
+  cudaError_t e = c->ops.set_state(c->p.pattern, 0, a, P, nullptr, nullptr, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
   c->t = 0;
   return LBM_OK;
@@ -385,7 +408,8 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
       if (e == cudaSuccess) c->cur = 1 - c->cur;
     } else {
       SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
-      const int kind = (c->t & 1) ? K_AA_ODD : K_AA_EVEN;
+      const bool odd = (c->t & 1) != 0;
+      const int kind = c->p.pattern == LBM_AA ? (odd ? K_AA_ODD : K_AA_EVEN) : (odd ? K_ESO_ODD : K_ESO_EVEN);
       set_interior(a, c, kind);
       e = c->ops.sweep(c->kernel_op, kind, c->has_mask, a, c->stream);
     }

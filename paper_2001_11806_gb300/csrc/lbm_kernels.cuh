@@ -27,8 +27,27 @@
 
 namespace lbm {
 
-enum Kind : int { K_PULL = 0, K_AA_EVEN = 1, K_AA_ODD = 2 };
-enum View : int { V_PULL = 0, V_AA_NATURAL = 1, V_AA_INVERTED = 2 };
+enum Kind : int { K_PULL = 0, K_AA_EVEN = 1, K_AA_ODD = 2, K_ESO_EVEN = 3, K_ESO_ODD = 4 };
+enum View : int { V_PULL = 0, V_AA_NATURAL = 1, V_AA_INVERTED = 2, V_ESO_EVEN = 3, V_ESO_ODD = 4 };
+
+// Esoteric twist (Sec. IV-B, single array run as even and odd kernels).  Cell
+// x owns the slots at x and at its positive neighbours: it reads f_q(x) from
+// location x + max(-c_q, 0) (componentwise; slot q after an even number of
+// steps, slot qbar after an odd number) and writes P_q(x) to location
+// x + max(c_q, 0) (slot qbar in the even kernel, q in the odd kernel), where
+// the cell x + c_q reads it in the next step.  Locations wrap on every axis;
+// on a non-periodic axis the wrapped pairs are kept apart by the boundary
+// rule: for a boundary link (x, qbar) the value B_qbar(P(x)) goes to the
+// other slot of the same location (q in the even kernel, qbar in the odd
+// one), which is the slot x reads f_qbar(x) from in the next step and which
+// the link's source would have written.
+__host__ __device__ constexpr int eso_rd(int c) { return c < 0 ? 1 : 0; }
+// Set by k_link_mask in its types word when a fluid cell lies in the last
+// layer (index n - 1) of a non-periodic axis.  The esoteric twist needs that
+// layer non-fluid: its wrapped locations are shared with the first layer,
+// whose boundary links would then race with the fluid cells there.
+constexpr unsigned TYPES_FLUID_LAST_LAYER = 1u << 8;
+__host__ __device__ constexpr int eso_wr(int c) { return c > 0 ? 1 : 0; }
 
 struct Geom {
   int nx, ny, nz;
@@ -90,6 +109,15 @@ __device__ __forceinline__ bool row_inner(const Geom& g, int y, int z) {
   const bool iy = unsigned(y - 1) < unsigned(g.ny - 2);
   if constexpr (L::D == 2) return iy;
   else return iy && unsigned(z - 1) < unsigned(g.nz - 2);
+}
+
+// The same for the esoteric twist, which only touches positive neighbours
+// (y <= ny - 2 and, in 3-D, z <= nz - 2).
+template <class L>
+__device__ __forceinline__ bool row_inner_eso(const Geom& g, int y, int z) {
+  const bool iy = unsigned(y) < unsigned(g.ny - 1);
+  if constexpr (L::D == 2) return iy;
+  else return iy && unsigned(z) < unsigned(g.nz - 1);
 }
 
 // Boundary type of the link whose source cell is (sx, sy, sz) (may lie one
@@ -262,10 +290,26 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
   const Nbr nb = make_nbr(a.g, x, y, z);
   T v[L::Q];
   // periodic sweeps of rows away from the y and z faces (uniform per block)
+  constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
   bool fast = false;
-  if constexpr (!BND && KIND != K_AA_EVEN) fast = row_inner<L>(a.g, y, z);
+  if constexpr (!BND && ESO) fast = row_inner_eso<L>(a.g, y, z);
+  else if constexpr (!BND && KIND != K_AA_EVEN) fast = row_inner<L>(a.g, y, z);
 
-  if constexpr (KIND == K_AA_EVEN) {
+  if constexpr (ESO) {
+    if (fast) {
+      const int ip = cell - (x == a.g.nx - 1 ? a.g.nx : 0);  // location x + 1 with the x wrap
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q)
+        v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[eso_rd(L::cx(q)) ? ip : cell], L::w(q));
+    } else {
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) {
+        const int qs = KIND == K_ESO_EVEN ? q : opp(q);
+        const int idx = nb.at(eso_rd(L::cx(q)), eso_rd(L::cy(q)), eso_rd(L::cz(q)));
+        v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
+      }
+    }
+  } else if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) v[q] = D::load(reinterpret_cast<const S*>(a.srcq[q])[cell], L::w(q));
   } else if (fast) {
@@ -329,6 +373,28 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
     if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
       for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
+    } else if constexpr (ESO) {
+      int tx;
+      asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+      const int xs = blockIdx.x * blockDim.x + tx;
+      if (fast) {
+        const int cs = xs + a.g.nx * (y + a.g.ny * z);
+        const int ip = cs - (xs == a.g.nx - 1 ? a.g.nx : 0);
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q)
+          reinterpret_cast<S*>(a.dsti[q])[eso_wr(L::cx(q)) ? ip : cs] = D::store(v[q], L::w(q));
+      } else {
+        const Nbr nbs = make_nbr(a.g, xs, y, z);
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) {
+          // even: qbar, odd: q; a boundary link (x, qbar) swaps to the other slot
+          const int p = opp(q);
+          const bool b = BND && ((mask >> p) & 1u);
+          const int qd = ((KIND == K_ESO_EVEN) != b) ? p : q;
+          const int idx = nbs.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)));
+          reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+        }
+      }
     } else {
       // The neighbour offsets of the stores are rebuilt from a fresh read of
       // %tid.x: an asm with side effects is not moved above the loads and its
@@ -454,6 +520,13 @@ __device__ void gather_f64(const SweepArgs& a, int view, int x, int y, int z, in
   const S* A = static_cast<const S*>(a.src);
   const long long N = a.g.N;
   const Nbr nb = make_nbr(a.g, x, y, z);
+  if (view == V_ESO_EVEN || view == V_ESO_ODD) {
+    for (int q = 0; q < L::Q; ++q) {
+      const int slot = view == V_ESO_EVEN ? q : opp(q);
+      f[q] = ST::to_f64(A[slot * N + nb.at(eso_rd(L::cx(q)), eso_rd(L::cy(q)), eso_rd(L::cz(q)))], L::w(q));
+    }
+    return;
+  }
   if (view == V_AA_NATURAL) {
     for (int q = 0; q < L::Q; ++q) f[q] = ST::to_f64(A[q * N + cell], L::w(q));
     return;
@@ -514,6 +587,13 @@ __device__ void gather_h(const SweepArgs& a, int view, int x, int y, int z, int 
   const S* A = static_cast<const S*>(a.src);
   const long long N = a.g.N;
   const Nbr nb = make_nbr(a.g, x, y, z);
+  if (view == V_ESO_EVEN || view == V_ESO_ODD) {
+    for (int q = 0; q < L::Q; ++q) {
+      const int slot = view == V_ESO_EVEN ? q : opp(q);
+      h[q] = ST::to_h(A[slot * N + nb.at(eso_rd(L::cx(q)), eso_rd(L::cy(q)), eso_rd(L::cz(q)))], L::w(q));
+    }
+    return;
+  }
   if (view == V_AA_NATURAL) {
     for (int q = 0; q < L::Q; ++q) h[q] = ST::to_h(A[q * N + cell], L::w(q));
     return;
@@ -678,6 +758,9 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsi
     }
     int x, y, z;
     cell_coords(a.g, cell, x, y, z);
+    if (types != nullptr && ((!a.g.per[0] && x == a.g.nx - 1) || (!a.g.per[1] && y == a.g.ny - 1) ||
+                             (!a.g.per[2] && z == a.g.nz - 1)))
+      atomicOr(types, TYPES_FLUID_LAST_LAYER);
     uint32_t m = 0;
     for (int q = 1; q < L::Q; ++q) {
       int sx = x - L::cx(q), sy = y - L::cy(q), sz = z - L::cz(q);
@@ -707,9 +790,11 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsi
 // parity): f_q(y) = P_q(y - c_q), so cell x pushes P_q(x) into slot q of
 // y = x + c_q, exactly like the stores of the odd step; when y is not fluid
 // the boundary value B_qbar(P(x)) goes to slot qbar of x instead.  Each slot
-// is written once; non-fluid cells write their own slots.
+// is written once; non-fluid cells write their own slots.  Esoteric-twist
+// layout (even parity): the writes of an odd esoteric-twist step; non-fluid
+// cells write nothing.
 template <class L, class ST, bool BND>
-__global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int aa, int src_kind, const double* P,
+__global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int layout, int src_kind, const double* P,
                                                        const double* rho, const double* u) {
   using T = typename ST::T;
   using S = typename ST::S;
@@ -735,7 +820,10 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int aa
       v[q] = T(L::w(q)) * (dr + r0 * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
     }
   }
-  if (!aa || (mask & MASK_SOLID)) {
+  // esoteric twist: a solid cell's locations hold slots of its fluid
+  // neighbours, so it writes nothing
+  if (layout == 2 && (mask & MASK_SOLID)) return;
+  if (layout == 0 || (mask & MASK_SOLID)) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = ST::from_h(v[q], L::w(q));
     return;
@@ -756,6 +844,17 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int aa
     }
   }
   const Nbr nb = make_nbr(a.g, x, y, z);
+  if (layout == 2) {
+    // the writes of an odd esoteric-twist step: slot q at x + max(c_q, 0)
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      const int p = opp(q);
+      const bool b = BND && ((mask >> p) & 1u);
+      const int idx = nb.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)));
+      reinterpret_cast<S*>(a.dstq[b ? p : q])[idx] = ST::from_h(v[q], L::w(q));
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < L::Q; ++q) {
     const int p = opp(q);
@@ -778,7 +877,7 @@ inline dim3 sweep_grid(const Geom& g) {
 
 template <class L, class ST, int OP, int KIND>
 cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
-  if constexpr (ST::ID == StF16S::ID) {
+  if constexpr (ST::ID == StF16S::ID && KIND <= K_AA_ODD) {
     if (!bnd && (a.g.nx % 2) == 0) {
       Geom half = a.g;
       half.nx = a.g.nx / 2;
@@ -799,6 +898,8 @@ cudaError_t launch_sweep_op(int kind, bool bnd, const SweepArgs& a, cudaStream_t
     case K_PULL: return launch_sweep_k<L, ST, OP, K_PULL>(bnd, a, s);
     case K_AA_EVEN: return launch_sweep_k<L, ST, OP, K_AA_EVEN>(bnd, a, s);
     case K_AA_ODD: return launch_sweep_k<L, ST, OP, K_AA_ODD>(bnd, a, s);
+    case K_ESO_EVEN: return launch_sweep_k<L, ST, OP, K_ESO_EVEN>(bnd, a, s);
+    case K_ESO_ODD: return launch_sweep_k<L, ST, OP, K_ESO_ODD>(bnd, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -175,7 +175,9 @@ extern "C" lbm_status lbm_reduce_noalloc(const lbm_params* p, const void* pdf, c
   if (p->stencil == LBM_D2Q9) { a.cp.F[2] = 0.0; a.cp.u_wall[2] = 0.0; }
   a.cp.incompressible = p->incompressible ? 1 : 0;
   a.cp.rho_out = p->rho_outlet;
-  const int view = p->pattern == LBM_PULL ? V_PULL : ((t & 1) ? V_AA_INVERTED : V_AA_NATURAL);
+  const int view = p->pattern == LBM_PULL       ? V_PULL
+                   : p->pattern == LBM_ESOTWIST ? ((t & 1) ? V_ESO_ODD : V_ESO_EVEN)
+                                                : ((t & 1) ? V_AA_INVERTED : V_AA_NATURAL);
   const int nblocks = (int)((N + noalloc::kChunk - 1) / noalloc::kChunk);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;

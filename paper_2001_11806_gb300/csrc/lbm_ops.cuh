@@ -39,12 +39,13 @@ struct Ops {
     k_reduce_partial<L, ST><<<nblocks, kRedThreads, 0, s>>>(a, view, partials);
     return cudaGetLastError();
   }
-  static cudaError_t set_state(bool aa, int src_kind, const SweepArgs& a, const double* P, const double* rho,
+  // layout: 0 two-grid (P in place), 1 AA natural, 2 esoteric twist even
+  static cudaError_t set_state(int layout, int src_kind, const SweepArgs& a, const double* P, const double* rho,
                                const double* u, cudaStream_t s) {
     if (a.mask != nullptr)
-      k_init_push<L, ST, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
+      k_init_push<L, ST, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, layout, src_kind, P, rho, u);
     else
-      k_init_push<L, ST, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, aa ? 1 : 0, src_kind, P, rho, u);
+      k_init_push<L, ST, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, layout, src_kind, P, rho, u);
     return cudaGetLastError();
   }
   using T = typename ST::T;
@@ -94,7 +95,7 @@ struct OpsTable {
   cudaError_t (*populations)(int, const SweepArgs&, double*, cudaStream_t);
   cudaError_t (*macroscopic)(int, const SweepArgs&, void*, void*, bool, cudaStream_t);
   cudaError_t (*reduce_partial)(int, const SweepArgs&, double*, int, cudaStream_t);
-  cudaError_t (*set_state)(bool, int, const SweepArgs&, const double*, const double*, const double*, cudaStream_t);
+  cudaError_t (*set_state)(int, int, const SweepArgs&, const double*, const double*, const double*, cudaStream_t);
   cudaError_t (*link_mask)(const SweepArgs&, uint32_t*, unsigned*, cudaStream_t);
   cudaError_t (*adjoint)(int, bool, const SweepArgs&, const void*, void*, double*, cudaStream_t);
   cudaError_t (*ke_seed)(bool, const SweepArgs&, const int*, double*, void*, double*, cudaStream_t);

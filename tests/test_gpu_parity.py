@@ -89,7 +89,7 @@ COMBOS = [(s, c) for s in ["D2Q9", "D3Q19", "D3Q27"] for c in ["srt", "trt", "mr
 
 @pytest.mark.parametrize("stencil,collision", COMBOS)
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
 @pytest.mark.parametrize("steps", [1, 4])
 def test_periodic_parity(stencil, collision, storage, pattern, steps):
     r = run_pair(stencil, collision, storage, pattern, _shape(stencil), steps)
@@ -100,7 +100,7 @@ def test_periodic_parity(stencil, collision, storage, pattern, steps):
 
 @pytest.mark.parametrize("stencil,collision", COMBOS)
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "f32s"])
-@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
 @pytest.mark.parametrize("steps", [3, 4])
 def test_channel_parity(stencil, collision, storage, pattern, steps):
     shape = _shape(stencil)
@@ -116,7 +116,7 @@ def test_channel_parity(stencil, collision, storage, pattern, steps):
 
 
 @pytest.mark.parametrize("stencil,collision", [c for c in COMBOS if c[1] not in ("cumulant", "kbc")])
-@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
 @pytest.mark.parametrize("incompressible", [False, True])
 def test_force_parity(stencil, collision, pattern, incompressible):
     shape = _shape(stencil)
@@ -141,41 +141,44 @@ def test_reduction_parity(stencil, collision):
 @pytest.mark.parametrize("stencil,collision", COMBOS)
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
 def test_aa_matches_two_grid_bitwise(stencil, collision, storage):
-    """Same arithmetic in both patterns: identical bits after an even number
-    of steps for FP64 and FP32 storage.  No-slip walls only: UBB and outlet
-    values are rounded to the storage type when written (AA) but not when read
-    (pull).  The two patterns are separate kernel instantiations, so the
-    compiler may round an FP32 intermediate differently; with FP16 storage
-    that can flip the last binary16 bit of a value, so FP16 is held to two
-    binary16 ulps of h = f - w."""
+    """Same arithmetic in all three patterns (pull, AA, esoteric twist):
+    identical bits after an even number of steps for FP64 and FP32 storage.
+    No-slip walls only: UBB and outlet values are rounded to the storage type
+    when written (AA, esoteric twist) but not when read (pull).  The patterns
+    are separate kernel instantiations, so the compiler may round an FP32
+    intermediate differently; with FP16 storage that can flip the last
+    binary16 bit of a value, so FP16 is held to two binary16 ulps of
+    h = f - w."""
     shape = _shape(stencil)
     fl = _flags(shape)
     fl[fl != 0] = olbm.NOSLIP
     lat = olat.get(stencil)
     P = inputs.random_pdfs(lat.w, shape[::-1], seed=9).reshape(lat.q, -1)
     out = []
-    for pattern in ["pull", "aa"]:
+    for pattern in ["pull", "aa", "eso"]:
         sim = Sim(stencil, collision, storage, pattern, shape, periodic=(False, False, True),
                   omega=OMEGAS[collision], u_wall=(0.05, 0.0, 0.0), flags=fl)
         sim.set_state(P)
         sim.step(6)
         out.append(sim.populations().cpu().numpy())
     fluid = fl.reshape(-1) == 0
-    a, b = out[0][:, fluid], out[1][:, fluid]
-    if storage != "f16s":
-        assert np.array_equal(a, b)
-    else:
-        h = np.abs(a - lat.w[:, None])
-        diff = np.abs(a - b)
-        frac = np.mean(diff > 0)
-        print(f"f16s AA vs pull: {frac:.2e} of values differ, max {diff.max():.2e}")
-        assert np.all(diff <= 2.0 ** -10 * h + 1e-7)
+    a = out[0][:, fluid]
+    for other in out[1:]:
+        b = other[:, fluid]
+        if storage != "f16s":
+            assert np.array_equal(a, b)
+        else:
+            h = np.abs(a - lat.w[:, None])
+            diff = np.abs(a - b)
+            frac = np.mean(diff > 0)
+            print(f"f16s vs pull: {frac:.2e} of values differ, max {diff.max():.2e}")
+            assert np.all(diff <= 2.0 ** -10 * h + 1e-7)
 
 
 def test_degenerate_domains():
     lat = olat.d3q19()
     # one periodic cell: every neighbour is the cell itself
-    for pattern in ["pull", "aa"]:
+    for pattern in ["pull", "aa", "eso"]:
         r = run_pair("D3Q19", "trt", "f64", pattern, (1, 1, 1), 3)
         assert np.abs(r["f"][0] - r["f"][1]).max() < 1e-14
     # a box that is entirely solid: nothing moves, reductions are zero
@@ -188,18 +191,19 @@ def test_degenerate_domains():
     # zero steps is a no-op and an isolated fluid cell only bounces back
     fl = np.full((3, 3, 3), olbm.NOSLIP, np.uint8)
     fl[1, 1, 1] = 0
-    for pattern in ["pull", "aa"]:
+    for pattern in ["pull", "aa", "eso"]:
         r = run_pair("D3Q19", "mrt", "f64", pattern, (3, 3, 3), 0, flags=fl)
         assert np.abs(r["f"][0] - r["f"][1]).max() < 1e-15
         r = run_pair("D3Q19", "mrt", "f64", pattern, (3, 3, 3), 5, flags=fl)
         assert np.abs(r["f"][0] - r["f"][1]).max() < 1e-14
 
 
-def test_checkpoint_restore_roundtrip():
+@pytest.mark.parametrize("pattern", ["aa", "eso"])
+def test_checkpoint_restore_roundtrip(pattern):
     shape = _shape("D3Q19", big=False)
     lat = olat.d3q19()
     P = inputs.random_pdfs(lat.w, shape[::-1], seed=2).reshape(19, -1)
-    sim = Sim("D3Q19", "trt", "f32", "aa", shape, omega=OMEGAS["trt"])
+    sim = Sim("D3Q19", "trt", "f32", pattern, shape, omega=OMEGAS["trt"])
     sim.set_state(P)
     sim.step(3)
     raw, t = sim.get_pdfs()
@@ -281,7 +285,7 @@ def test_f16_two_cell_kernel_parity(stencil, collision, pattern, nx):
 @pytest.mark.parametrize("stencil", ["D2Q9", "D3Q19", "D3Q27"])
 @pytest.mark.parametrize("collision,magic", [("srt", None), ("trt", None), ("trt", 3 / 16)])
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
-@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
 def test_smagorinsky_parity(stencil, collision, magic, storage, pattern):
     """Per-cell Smagorinsky rate (C_S = 0.17) on random populations with walls,
     an inlet, an outlet and a body force."""
@@ -308,14 +312,15 @@ def test_smagorinsky_parity(stencil, collision, magic, storage, pattern):
 
 @pytest.mark.parametrize("stencil", ["D2Q9", "D3Q19", "D3Q27"])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_kbc_incompressible_and_two_rate_form(stencil, storage):
+@pytest.mark.parametrize("pattern", ["aa", "eso"])
+def test_kbc_incompressible_and_two_rate_form(stencil, storage, pattern):
     """KBC with the incompressible equilibrium, and with omega_b = omega_s
     (the paper's two-rate form), walls and a moving inlet."""
     lat = olat.get(stencil)
     shape = _shape(stencil)
     fl = _flags(shape)
     for om, inc in (([1.95, 1.95], False), ([1.6, 0.7], True)):
-        sim = Sim(stencil, "kbc", storage, "aa", shape, periodic=(False, False, True), omega=om,
+        sim = Sim(stencil, "kbc", storage, pattern, shape, periodic=(False, False, True), omega=om,
                   incompressible=inc, u_wall=(0.05, 0.0, 0.0), flags=fl)
         P = inputs.random_pdfs(lat.w, shape[::-1], amp=0.05, seed=31)
         sim.set_state(P.reshape(lat.q, -1))
@@ -337,3 +342,39 @@ def test_kbc_unsupported_combinations():
         Sim("D3Q19", "kbc", "f32", "pull", (8, 8, 8), omega=[1.9, 1.0], force=(1e-4, 0.0, 0.0))
     with pytest.raises(LbmError):
         Sim("D3Q19", "kbc", "f32", "pull", (8, 8, 8), omega=[1.9, 1.0], smagorinsky_cs=0.1)
+
+
+def test_esotwist_refuses_fluid_last_layer():
+    """The esoteric twist wraps its locations on every axis, so along a
+    non-periodic axis the last layer must be non-fluid (LBM_E_UNSUPPORTED
+    otherwise); the first layer may be fluid."""
+    from paper_2001_11806_gb300 import LbmError
+    shape = (8, 6, 5)
+    fl = np.zeros(shape[::-1], np.uint8)
+    fl[:, -1, :] = olbm.NOSLIP
+    Sim("D3Q19", "trt", "f32", "eso", shape, periodic=(True, False, True), omega=[1.5, 1.2], flags=fl).close()
+    for per in [(True, False, True), (True, True, False)]:
+        bad = np.zeros(shape[::-1], np.uint8)
+        if not per[1]:
+            bad[:, 0, :] = olbm.NOSLIP
+        with pytest.raises(LbmError) as e:
+            Sim("D3Q19", "trt", "f32", "eso", shape, periodic=per, omega=[1.5, 1.2], flags=bad)
+        assert e.value.status == 2
+    with pytest.raises(LbmError) as e:
+        Sim("D3Q19", "trt", "f32", "eso", shape, periodic=(False, True, True), omega=[1.5, 1.2])
+    assert e.value.status == 2
+
+
+@pytest.mark.parametrize("stencil,collision", [("D2Q9", "srt"), ("D3Q19", "trt"), ("D3Q27", "cumulant")])
+def test_esotwist_channel_with_open_first_layer(stencil, collision):
+    """Fluid first layer against a wall-only last layer: the first layer's
+    boundary links read the wrapped locations of the solid last layer."""
+    lat = olat.get(stencil)
+    shape = _shape(stencil)
+    fl = np.zeros(shape[::-1], np.uint8)
+    fl[:, -1, :] = olbm.NOSLIP
+    fl[..., -1] = olbm.OUTLET
+    r = run_pair(stencil, collision, "f64", "eso", shape, 5, periodic=(False, False, True), flags=fl,
+                 u_wall=(0.05, 0.0, 0.0))
+    ef, er, eu = _errs(r)
+    assert ef < 1e-12 and er < 1e-12 and eu < 1e-12, (ef, er, eu)

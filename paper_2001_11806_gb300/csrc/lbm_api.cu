@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_ops.cuh"
@@ -65,6 +66,8 @@ struct lbm_ctx {
   double* partials = nullptr;
   double* result = nullptr;
   bool has_mask = false;
+  int* list = nullptr;  // fluid cells of a masked domain (SweepArgs::list)
+  int n_main = 0, n_wrap = 0;
   unsigned link_types = 0;  // OR of the boundary-link types present (L_INLET, L_OUTLET)
   cudaStream_t stream = nullptr;
   int64_t t = 0;
@@ -80,7 +83,8 @@ const char* kStatusNames[] = {"LBM_OK", "LBM_E_INVAL", "LBM_E_UNSUPPORTED", "LBM
                               "LBM_E_BUFSIZE", "LBM_E_NONFINITE", "LBM_E_BOUNDS", "LBM_E_STATE"};
 
 struct Layout {
-  size_t mask_off, mask_bytes, part_off, res_off, total;
+  size_t mask_off, mask_bytes, list_off, count_off, part_off, res_off, total;
+  int nblk;  // chunks of the fluid-list builder
 };
 
 int stencil_q(int s) { return s == LBM_D2Q9 ? 9 : (s == LBM_D3Q19 ? 19 : 27); }
@@ -96,13 +100,19 @@ bool needs_mask(const lbm_params& p, bool has_flags) {
   return false;
 }
 
-// aux = [link mask: 4 N bytes][reduction partials][reduction result]; the
-// mask region is always reserved so that the size does not depend on flags.
+// aux = [link mask: 4 N bytes][fluid-cell list: 4 N bytes][list-builder
+// counts: 2 x 4 x nblk bytes][reduction partials][reduction result]; the mask
+// and list regions are always reserved so that the size does not depend on
+// the flags.
 Layout layout_for(const lbm_params& p, long long N) {
+  (void)p;
   Layout l;
+  l.nblk = int((N + kListChunk - 1) / kListChunk);
   l.mask_off = 0;
   l.mask_bytes = align256(size_t(N) * 4);
-  l.part_off = l.mask_bytes;
+  l.list_off = l.mask_bytes;
+  l.count_off = l.list_off + align256(size_t(N) * 4);
+  l.part_off = l.count_off + align256(size_t(l.nblk) * 2 * sizeof(int));
   l.res_off = l.part_off + align256(size_t(kRedMaxBlocks) * 5 * sizeof(double));
   l.total = l.res_off + 256;
   return l;
@@ -177,6 +187,41 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
   return LBM_OK;
 }
 
+// Fluid-cell list of a masked domain (see k_sweep_list): per-chunk counts on
+// the device, exclusive offsets on the host, ordered scatter on the device.
+lbm_status build_list(lbm_ctx* c, const SweepArgs& a, const Layout& lay) {
+  int* counts = reinterpret_cast<int*>(static_cast<char*>(c->aux) + lay.count_off);
+  const int nblk = lay.nblk;
+  cudaError_t e = c->ops.list_count(a, nblk, counts, c->stream);
+  std::vector<int> h(size_t(nblk) * 2);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), counts, h.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("list count: ") + cudaGetErrorString(e);
+    return LBM_E_CUDA;
+  }
+  long long n_main = 0;
+  for (int b = 0; b < nblk; ++b) n_main += h[b];
+  long long run1 = 0, run2 = n_main;
+  for (int b = 0; b < nblk; ++b) {
+    const int k1 = h[b], k2 = h[size_t(nblk) + b];
+    h[b] = int(run1);
+    h[size_t(nblk) + b] = int(run2);
+    run1 += k1;
+    run2 += k2;
+  }
+  c->n_main = int(n_main);
+  c->n_wrap = int(run2 - n_main);
+  e = cudaMemcpyAsync(counts, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = c->ops.list_scatter(a, nblk, counts, c->list, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("list scatter: ") + cudaGetErrorString(e);
+    return LBM_E_CUDA;
+  }
+  return LBM_OK;
+}
+
 lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
   c->err = std::string(where) + ": " + cudaGetErrorString(e);
   return LBM_E_CUDA;
@@ -195,6 +240,9 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
   if (c->d == 2) a.g.per[2] = 1;
   a.g.N = c->N;
   a.cp = c->cp;
+  a.list = c->list;
+  a.n_main = c->n_main;
+  a.n_wrap = c->n_wrap;
   for (int q = 0; q < 27; ++q) {
     const size_t off = q < c->q ? size_t(q) * size_t(c->N) * c->elem : 0;
     a.srcq[q] = src ? static_cast<const char*>(src) + off : nullptr;
@@ -365,6 +413,12 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
     if (p->pattern == LBM_ESOTWIST && (c->link_types & TYPES_FLUID_LAST_LAYER)) {
       delete c;
       return LBM_E_UNSUPPORTED;
+    }
+    c->list = reinterpret_cast<int*>(static_cast<char*>(aux) + lay.list_off);
+    const lbm_status ls = build_list(c, a, lay);
+    if (ls != LBM_OK) {
+      delete c;
+      return ls;
     }
   }
   *out = c;

@@ -75,6 +75,10 @@ struct SweepArgs {
   // x wrap), as the AA even sweep does.
   const char* srci[27];
   char* dsti[27];
+  // masked domains: fluid cells in ascending order, n_main without wrapped
+  // neighbour accesses followed by n_wrap with
+  const int* list;
+  int n_main, n_wrap;
 };
 
 constexpr int kBlockX = 128;
@@ -267,12 +271,9 @@ __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, st
 }
 
 // ------------------------------------------------------------------- sweep
-// Boundary links are handled without branching on the common path: a
-// boundary link only changes which slot is read (pull, AA odd) or written (AA
-// odd), so the address is selected.  Inlet and outlet links, which also change
-// the value, exist only in cells flagged MASK_SPECIAL and are fixed up in a
-// rare divergent branch.
-template <class L, class ST, int OP, int KIND, bool BND>
+// Fully periodic domains without flags: one thread per cell, 128-thread
+// blocks along x, grid (nx/128, ny, nz).
+template <class L, class ST, int OP, int KIND>
 __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
   using T = typename ST::T;
   using S = typename ST::S;
@@ -282,18 +283,14 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
   if (x >= a.g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   const int cell = x + a.g.nx * (y + a.g.ny * z);
-  uint32_t mask = 0;
-  if constexpr (BND) {
-    mask = a.mask[cell];
-    if (mask & MASK_SOLID) return;
-  }
   const Nbr nb = make_nbr(a.g, x, y, z);
   T v[L::Q];
-  // periodic sweeps of rows away from the y and z faces (uniform per block)
+  // rows away from the y and z faces (uniform per block) use the shifted
+  // stream bases with a per-thread x wrap
   constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
   bool fast = false;
-  if constexpr (!BND && ESO) fast = row_inner_eso<L>(a.g, y, z);
-  else if constexpr (!BND && KIND != K_AA_EVEN) fast = row_inner<L>(a.g, y, z);
+  if constexpr (ESO) fast = row_inner_eso<L>(a.g, y, z);
+  else if constexpr (KIND != K_AA_EVEN) fast = row_inner<L>(a.g, y, z);
 
   if constexpr (ESO) {
     if (fast) {
@@ -322,27 +319,11 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
       v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[idx], L::w(q));
     }
   } else {
-    // pull:   fluid source -> P_q(x - c_q) = src[q][x - c_q];  boundary -> P_qbar(x) = src[qbar][x]
-    // AA odd: fluid source -> A[qbar][x - c_q];                 boundary -> A[q][x]
+    // pull: P_q(x - c_q) = src[q][x - c_q];  AA odd: A[qbar][x - c_q]
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) {
-      const bool b = BND && ((mask >> q) & 1u);
-      const int qs = (KIND == K_PULL) ? (b ? opp(q) : q) : (b ? q : opp(q));
-      const int idx = b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
-      v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
-    }
-    if constexpr (KIND == K_PULL && BND) {
-      if (mask & MASK_SPECIAL) {
-        const OutletP op = outlet_params(a.cp);
-        for (int q = 1; q < L::Q; ++q) {
-          if ((mask >> q) & 1u) {
-            const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
-            const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
-                                                L::cz(q) * a.cp.u_wall[2]);
-            v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb);
-          }
-        }
-      }
+      const int qs = KIND == K_PULL ? q : opp(q);
+      v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[nb.at(-L::cx(q), -L::cy(q), -L::cz(q))], L::w(q));
     }
   }
 
@@ -351,80 +332,294 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
   if constexpr (KIND == K_PULL) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = D::store(v[q], L::w(q));
-  } else {
-    if constexpr (BND) {
-      // inlet/outlet links (x, p = qbar): the slot A[p][x] receives B_p(P(x))
-      // instead of P_q(x); no-slip links keep P_q(x) = B_p(P(x)) unchanged
-      if (mask & MASK_SPECIAL) {
-        const OutletP op = outlet_params(a.cp);
-        T up[3];
-        post_velocity<L, T, DH>(v, op, up);
+  } else if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
-        for (int q = 1; q < L::Q; ++q) {
-          const int p = opp(q);
-          if ((mask >> p) & 1u) {
-            const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
-            if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
-            else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
-          }
+    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
+  } else {
+    // The store offsets are rebuilt from a fresh read of %tid.x: an asm with
+    // side effects is not moved above the loads and its result cannot be
+    // merged with the offsets of the load phase, so the offsets are not held
+    // in registers across the collision.
+    int tx;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+    const int xs = blockIdx.x * blockDim.x + tx;
+    const int cs = xs + a.g.nx * (y + a.g.ny * z);
+    if (fast) {
+      // x + c_q with the x wrap: c_x = +1 writes x + 1 (wraps at nx - 1), c_x = -1 writes x - 1
+      const int ip = cs - (xs == a.g.nx - 1 ? a.g.nx : 0);
+      const int im = cs + (xs == 0 ? a.g.nx : 0);
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) {
+        const int idx = ESO ? (eso_wr(L::cx(q)) ? ip : cs) : (L::cx(q) > 0 ? ip : (L::cx(q) < 0 ? im : cs));
+        reinterpret_cast<S*>(a.dsti[q])[idx] = D::store(v[q], L::w(q));
+      }
+    } else {
+      const Nbr nbs = make_nbr(a.g, xs, y, z);
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) {
+        // AA odd: A[q][x + c_q];  esoteric twist: slot qbar (even) or q (odd) at x + max(c_q, 0)
+        const int qd = KIND == K_ESO_EVEN ? opp(q) : q;
+        const int idx = ESO ? nbs.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)))
+                            : nbs.at(L::cx(q), L::cy(q), L::cz(q));
+        reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& x, int& y, int& z) {
+  x = (int)(cell % g.nx);
+  const long long r = cell / g.nx;
+  y = (int)(r % g.ny);
+  z = (int)(r / g.ny);
+}
+
+// ------------------------------------------------------- fluid-cell lists
+// Domains with a link mask (flags or a non-periodic axis) are swept over the
+// list of their fluid cells in ascending order, so no warp carries lanes of
+// solid cells (in a porous channel most warps would).  The list holds the
+// plain cells first (n_main of them: no neighbour access wraps around a
+// periodic axis, no inlet or outlet link) and then the others (n_wrap),
+// which a second launch sweeps with coordinate-based addressing and the
+// inlet/outlet fix-ups, so the main launch has neither.  A no-slip link only
+// changes which slot is read (pull, AA odd) or written (AA odd, esoteric
+// twist), so the address is selected without branching.
+
+// 0: not fluid; 1: plain (no wrapped neighbour access, no inlet or outlet
+// link); 2: on a face of a periodic axis or with an inlet or outlet link
+template <class L>
+__device__ __forceinline__ int list_category(const SweepArgs& a, long long cell) {
+  const uint32_t m = a.mask[cell];
+  if (m & MASK_SOLID) return 0;
+  if (m & MASK_SPECIAL) return 2;
+  int x, y, z;
+  cell_coords(a.g, cell, x, y, z);
+  bool wrap = (a.g.per[0] && (x == 0 || x == a.g.nx - 1)) || (a.g.per[1] && (y == 0 || y == a.g.ny - 1));
+  if constexpr (L::D == 3) wrap = wrap || (a.g.per[2] && (z == 0 || z == a.g.nz - 1));
+  return wrap ? 2 : 1;
+}
+
+constexpr int kListThreads = 256;
+constexpr int kListChunk = 4 * kListThreads;  // cells per block of the list builder
+
+// counts[b] and counts[nblk + b]: main and wrap cells of chunk b
+template <class L>
+__global__ void __launch_bounds__(kListThreads) k_list_count(const SweepArgs a, int nblk, int* __restrict__ counts) {
+  __shared__ int sm[2];
+  if (threadIdx.x < 2) sm[threadIdx.x] = 0;
+  __syncthreads();
+  int c1 = 0, c2 = 0;
+  for (int k = 0; k < 4; ++k) {
+    const long long cell = (long long)blockIdx.x * kListChunk + k * kListThreads + threadIdx.x;
+    if (cell < a.g.N) {
+      const int cat = list_category<L>(a, cell);
+      c1 += cat == 1;
+      c2 += cat == 2;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+    c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sm[0], c1);
+    atomicAdd(&sm[1], c2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    counts[blockIdx.x] = sm[0];
+    counts[nblk + blockIdx.x] = sm[1];
+  }
+}
+
+// Writes each chunk's cells at its exclusive offsets (offsets[b] for main
+// cells, offsets[nblk + b] for wrap cells, both absolute), in ascending order.
+template <class L>
+__global__ void __launch_bounds__(kListThreads) k_list_scatter(const SweepArgs a, int nblk,
+                                                                const int* __restrict__ offsets, int* __restrict__ list) {
+  __shared__ int warp_tot[2][kListThreads / 32];
+  int base1 = offsets[blockIdx.x], base2 = offsets[nblk + blockIdx.x];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 4; ++k) {
+    const long long cell = (long long)blockIdx.x * kListChunk + k * kListThreads + threadIdx.x;
+    const int cat = cell < a.g.N ? list_category<L>(a, cell) : 0;
+    const unsigned m1 = __ballot_sync(0xffffffffu, cat == 1), m2 = __ballot_sync(0xffffffffu, cat == 2);
+    const unsigned below = (1u << lane) - 1u;
+    if (lane == 0) {
+      warp_tot[0][wid] = __popc(m1);
+      warp_tot[1][wid] = __popc(m2);
+    }
+    __syncthreads();
+    int pre1 = 0, pre2 = 0, tot1 = 0, tot2 = 0;
+    for (int w = 0; w < kListThreads / 32; ++w) {
+      if (w < wid) { pre1 += warp_tot[0][w]; pre2 += warp_tot[1][w]; }
+      tot1 += warp_tot[0][w];
+      tot2 += warp_tot[1][w];
+    }
+    if (cat == 1) list[base1 + pre1 + __popc(m1 & below)] = (int)cell;
+    if (cat == 2) list[base2 + pre2 + __popc(m2 & below)] = (int)cell;
+    base1 += tot1;
+    base2 += tot2;
+    __syncthreads();
+  }
+}
+
+// Sweep over list[0, n_main) (WRAP = false: every neighbour access is the
+// cell's own index plus a fixed offset) or over list[n_main, n_main + n_wrap)
+// (WRAP = true: neighbour indices from the coordinates, with wrapping, and the
+// inlet/outlet fix-ups).
+template <class L, class ST, int OP, int KIND, bool WRAP>
+__global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
+  using T = typename ST::T;
+  using S = typename ST::S;
+  constexpr bool DH = dom_h<ST, OP>();
+  using D = Dom<ST, DH>;
+  constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (WRAP ? a.n_wrap : a.n_main)) return;
+  const int cell = a.list[WRAP ? a.n_main + i : i];
+  const uint32_t mask = a.mask[cell];
+  T v[L::Q];
+  if constexpr (WRAP) {
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    const Nbr nb = make_nbr(a.g, x, y, z);
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      // pull:   fluid source -> src[q][x - c_q];  boundary -> src[qbar][x]
+      // AA odd: fluid source -> A[qbar][x - c_q]; boundary -> A[q][x]
+      // esoteric twist: slot q (even) or qbar (odd) at x + max(-c_q, 0)
+      const bool b = (mask >> q) & 1u;
+      int qs, idx;
+      if constexpr (ESO) {
+        qs = KIND == K_ESO_EVEN ? q : opp(q);
+        idx = nb.at(eso_rd(L::cx(q)), eso_rd(L::cy(q)), eso_rd(L::cz(q)));
+      } else if constexpr (KIND == K_AA_EVEN) {
+        qs = q;
+        idx = cell;
+      } else {
+        qs = KIND == K_PULL ? (b ? opp(q) : q) : (b ? q : opp(q));
+        idx = b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+      }
+      v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
+    }
+  } else {
+    // The two slots a direction can touch, q and qbar, are adjacent streams:
+    // one base (the lower slot) and an unsigned 32-bit element offset that
+    // adds N for the upper one (cell +- c_q stays inside the box here, and
+    // 2 N - 1 < 2^32).
+    const unsigned N = unsigned(a.g.N);
+    const int nx = a.g.nx, nxy = a.g.nx * a.g.ny;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      const bool b = (mask >> q) & 1u;
+      if constexpr (ESO) {
+        v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[cell], L::w(q));
+      } else if constexpr (KIND == K_AA_EVEN) {
+        v[q] = D::load(reinterpret_cast<const S*>(a.srcq[q])[cell], L::w(q));
+      } else {
+        // pull: fluid src[q][x - c_q], boundary src[qbar][x];
+        // AA odd: fluid A[qbar][x - c_q], boundary A[q][x]
+        const int lo = q < opp(q) ? q : opp(q);
+        const int sf = KIND == K_PULL ? q : opp(q), sb = KIND == K_PULL ? opp(q) : q;
+        const int off = L::cx(q) + nx * L::cy(q) + nxy * L::cz(q);
+        const unsigned idx = unsigned(b ? cell : cell - off) + ((b ? sb : sf) != lo ? N : 0u);
+        v[q] = D::load(reinterpret_cast<const S*>(a.srcq[lo])[idx], L::w(q));
+      }
+    }
+  }
+  if constexpr (KIND == K_PULL && WRAP) {
+    if (mask & MASK_SPECIAL) {
+      int x, y, z;
+      cell_coords(a.g, cell, x, y, z);
+      const OutletP op = outlet_params(a.cp);
+      for (int q = 1; q < L::Q; ++q) {
+        if ((mask >> q) & 1u) {
+          const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+          const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
+                                              L::cz(q) * a.cp.u_wall[2]);
+          v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb);
         }
       }
     }
-    if constexpr (KIND == K_AA_EVEN) {
+  }
+
+  collide<L, T, DH>(v, a.cp, std::integral_constant<int, OP>{});
+
+  if constexpr (KIND != K_PULL && WRAP) {
+    // inlet/outlet links (x, p = qbar): the value written for direction q is
+    // B_p(P(x)) instead of P_q(x); no-slip links keep P_q(x) = B_p(P(x))
+    if (mask & MASK_SPECIAL) {
+      int x, y, z;
+      cell_coords(a.g, cell, x, y, z);
+      const OutletP op = outlet_params(a.cp);
+      T up[3];
+      post_velocity<L, T, DH>(v, op, up);
 #pragma unroll
-      for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
-    } else if constexpr (ESO) {
-      int tx;
-      asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
-      const int xs = blockIdx.x * blockDim.x + tx;
-      if (fast) {
-        const int cs = xs + a.g.nx * (y + a.g.ny * z);
-        const int ip = cs - (xs == a.g.nx - 1 ? a.g.nx : 0);
-#pragma unroll
-        for (int q = 0; q < L::Q; ++q)
-          reinterpret_cast<S*>(a.dsti[q])[eso_wr(L::cx(q)) ? ip : cs] = D::store(v[q], L::w(q));
-      } else {
-        const Nbr nbs = make_nbr(a.g, xs, y, z);
-#pragma unroll
-        for (int q = 0; q < L::Q; ++q) {
-          // even: qbar, odd: q; a boundary link (x, qbar) swaps to the other slot
-          const int p = opp(q);
-          const bool b = BND && ((mask >> p) & 1u);
-          const int qd = ((KIND == K_ESO_EVEN) != b) ? p : q;
-          const int idx = nbs.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)));
-          reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+      for (int q = 1; q < L::Q; ++q) {
+        const int p = opp(q);
+        if ((mask >> p) & 1u) {
+          const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+          if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
+          else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
         }
       }
-    } else {
-      // The neighbour offsets of the stores are rebuilt from a fresh read of
-      // %tid.x: an asm with side effects is not moved above the loads and its
-      // result cannot be merged with the offsets of the load phase, so the
-      // offsets are not held in registers across the collision.
-      int tx;
-      asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
-      const int xs = blockIdx.x * blockDim.x + tx;
-      if (fast) {
-        // x + c_q with the x wrap: c_x = +1 writes x + 1 (wraps at nx - 1), c_x = -1 writes x - 1
-        const int cs = xs + a.g.nx * (y + a.g.ny * z);
-        const int ip = cs - (xs == a.g.nx - 1 ? a.g.nx : 0);
-        const int im = cs + (xs == 0 ? a.g.nx : 0);
+    }
+  }
+  if constexpr (KIND == K_PULL) {
 #pragma unroll
-        for (int q = 0; q < L::Q; ++q) {
-          const int idx = L::cx(q) > 0 ? ip : (L::cx(q) < 0 ? im : cs);
-          reinterpret_cast<S*>(a.dsti[q])[idx] = D::store(v[q], L::w(q));
-        }
+    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = D::store(v[q], L::w(q));
+  } else if constexpr (KIND == K_AA_EVEN) {
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
+  } else if constexpr (WRAP) {
+    int x, y, z;
+    cell_coords(a.g, cell, x, y, z);
+    const Nbr nbs = make_nbr(a.g, x, y, z);
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      // AA odd: fluid destination -> A[q][x + c_q]; boundary link (x, qbar) -> A[qbar][x]
+      // esoteric twist: slot qbar (even) or q (odd) at x + max(c_q, 0); a
+      // boundary link (x, qbar) takes the other slot
+      const int p = opp(q);
+      const bool b = (mask >> p) & 1u;
+      int qd, idx;
+      if constexpr (ESO) {
+        qd = ((KIND == K_ESO_EVEN) != b) ? p : q;
+        idx = nbs.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)));
       } else {
-        const Nbr nbs = make_nbr(a.g, xs, y, z);
-#pragma unroll
-        for (int q = 0; q < L::Q; ++q) {
-          // AA odd: fluid destination -> A[q][x + c_q]; boundary -> A[p][x]
-          const int p = opp(q);
-          const bool b = BND && ((mask >> p) & 1u);
-          const int qd = b ? p : q;
-          const int idx = b ? cell : nbs.at(L::cx(q), L::cy(q), L::cz(q));
-          reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
-        }
+        qd = b ? p : q;
+        idx = b ? cell : nbs.at(L::cx(q), L::cy(q), L::cz(q));
       }
+      reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+    }
+  } else {
+    // cell and mask are read again (cache hits) rather than held across the
+    // collision: an asm with side effects is not hoisted above it
+    int tx;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+    const int cs = a.list[blockIdx.x * blockDim.x + tx];
+    const uint32_t ms = a.mask[cs];
+    const unsigned N = unsigned(a.g.N);
+    const int nx = a.g.nx, nxy = a.g.nx * a.g.ny;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      const int p = opp(q);
+      const bool b = (ms >> p) & 1u;
+      const int lo = q < p ? q : p;
+      unsigned idx;
+      if constexpr (ESO) {
+        // slot qbar (even) or q (odd) at x + max(c_q, 0); a boundary link
+        // takes the other slot of the same location
+        const int sn = KIND == K_ESO_EVEN ? p : q, sb = KIND == K_ESO_EVEN ? q : p;
+        const int wr = eso_wr(L::cx(q)) + nx * eso_wr(L::cy(q)) + nxy * eso_wr(L::cz(q));
+        idx = unsigned(cs + wr) + ((b ? sb : sn) != lo ? N : 0u);
+      } else {
+        // AA odd: fluid A[q][x + c_q], boundary A[qbar][x]
+        const int off = L::cx(q) + nx * L::cy(q) + nxy * L::cz(q);
+        idx = unsigned(b ? cs : cs + off) + ((b ? p : q) != lo ? N : 0u);
+      }
+      reinterpret_cast<S*>(a.dstq[lo])[idx] = D::store(v[q], L::w(q));
     }
   }
 }
@@ -640,13 +835,6 @@ __device__ __forceinline__ void moments_f64(const double (&f)[L::Q], const Colli
   const double inv = 1.0 / rho0;
   for (int d = 0; d < 3; ++d) u[d] = j[d] * inv;
   if (L::D == 2) u[2] = 0.0;
-}
-
-__device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& x, int& y, int& z) {
-  x = (int)(cell % g.nx);
-  const long long r = cell / g.nx;
-  y = (int)(r % g.ny);
-  z = (int)(r / g.ny);
 }
 
 template <class L, class ST>
@@ -885,10 +1073,14 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       return cudaGetLastError();
     }
   }
-  if (bnd)
-    k_sweep<L, ST, OP, KIND, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
-  else
-    k_sweep<L, ST, OP, KIND, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
+  if (!bnd) {
+    k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (a.n_main > 0) k_sweep_list<L, ST, OP, KIND, false><<<(a.n_main + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.n_wrap > 0) k_sweep_list<L, ST, OP, KIND, true><<<(a.n_wrap + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(a);
   return cudaGetLastError();
 }
 

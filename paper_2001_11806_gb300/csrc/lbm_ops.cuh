@@ -88,6 +88,18 @@ cudaError_t launch_link_mask(const SweepArgs& a, uint32_t* mask, unsigned* types
   return cudaGetLastError();
 }
 
+template <class L>
+cudaError_t launch_list_count(const SweepArgs& a, int nblk, int* counts, cudaStream_t s) {
+  k_list_count<L><<<nblk, kListThreads, 0, s>>>(a, nblk, counts);
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t launch_list_scatter(const SweepArgs& a, int nblk, const int* offsets, int* list, cudaStream_t s) {
+  k_list_scatter<L><<<nblk, kListThreads, 0, s>>>(a, nblk, offsets, list);
+  return cudaGetLastError();
+}
+
 // Dispatch table of one (stencil, storage) pair.  Each lbm_inst_*.cu defines
 // one factory returning it, so the C ABI unit instantiates no kernels.
 struct OpsTable {
@@ -100,13 +112,16 @@ struct OpsTable {
   cudaError_t (*adjoint)(int, bool, const SweepArgs&, const void*, void*, double*, cudaStream_t);
   cudaError_t (*ke_seed)(bool, const SweepArgs&, const int*, double*, void*, double*, cudaStream_t);
   cudaError_t (*eq_vjp)(const SweepArgs&, const double*, const double*, const void*, double*, cudaStream_t);
+  cudaError_t (*list_count)(const SweepArgs&, int, int*, cudaStream_t);
+  cudaError_t (*list_scatter)(const SweepArgs&, int, const int*, int*, cudaStream_t);
 };
 
 template <class L, class ST>
 OpsTable make_table() {
   return OpsTable{&Ops<L, ST>::sweep,          &Ops<L, ST>::populations, &Ops<L, ST>::macroscopic,
                   &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>,
-                  &Ops<L, ST>::adjoint,        &Ops<L, ST>::ke_seed,     &Ops<L, ST>::eq_vjp};
+                  &Ops<L, ST>::adjoint,        &Ops<L, ST>::ke_seed,     &Ops<L, ST>::eq_vjp,
+                  &launch_list_count<L>,       &launch_list_scatter<L>};
 }
 
 #define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();

@@ -9,9 +9,11 @@ larger than the 129 MB L2, so no flush is needed between timed steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 The line also carries "variants" (the other workloads of the metric: two-grid
-pull, FP16-shifted storage, the MRT channel, the D3Q27 cumulant, D2Q9 FP64 and
-the adjoint step against the forward step) and "accuracy" (FP32 and
-FP16-shifted storage against an FP64 run of the same kernels).
+pull, esoteric twist, FP16-shifted storage, Smagorinsky, KBC, the MRT channel,
+the D3Q27 cumulant, D2Q9 FP64 and the adjoint step against the forward step)
+and "accuracy" (FP32 and FP16-shifted storage against FP64 runs of the same
+kernels on the TGV, the channel and the cumulant TGV, with kinetic-energy
+decay).
 
 --impl reference times the FP64 numpy oracle on the host cores on a bounded
 sample of the same workload (a 32^3 periodic box per step).  Under torchrun
@@ -247,8 +249,14 @@ def run_variants(device, peak):
                                                        shape=(512, 128, 128), omega=[1.7, 1.0, 1.0, 1.0],
                                                        periodic=(False, False, False), u_wall=(0.05, 0, 0)),
          "channel", 300),
-        ("D3Q19 MRT FP16-shifted channel 512x128x128 pull", dict(stencil="D3Q19", collision="mrt", storage="f16s",
-                                                                 pattern="pull", shape=(512, 128, 128),
+        ("D3Q19 MRT FP32 channel 512x128x128 two-grid pull", dict(stencil="D3Q19", collision="mrt", storage="f32",
+                                                                  pattern="pull", shape=(512, 128, 128),
+                                                                  omega=[1.7, 1.0, 1.0, 1.0],
+                                                                  periodic=(False, False, False),
+                                                                  u_wall=(0.05, 0, 0)),
+         "channel", 300),
+        ("D3Q19 MRT FP16-shifted channel 512x128x128 AA", dict(stencil="D3Q19", collision="mrt", storage="f16s",
+                                                                 pattern="aa", shape=(512, 128, 128),
                                                                  omega=[1.7, 1.0, 1.0, 1.0],
                                                                  periodic=(False, False, False), u_wall=(0.05, 0, 0)),
          "channel", 300),
@@ -315,37 +323,92 @@ def run_variants(device, peak):
     return out
 
 
+def _rel_errors(fields, ref, mask=None):
+    """Relative L2 of rho - 1 and (worst component) of u against ref."""
+    r, v = fields
+    r64, u64 = ref
+    if mask is not None:
+        r, v, r64, u64 = r[mask], v[:, mask], r64[mask], u64[:, mask]
+    return {"rho_minus_1": float(np.linalg.norm(r - r64) / np.linalg.norm(r64 - 1.0)),
+            "u": float(max(np.linalg.norm(v[a] - u64[a]) / np.linalg.norm(u64[a]) for a in range(v.shape[0])))}
+
+
 def run_accuracy(device):
     """FP32 and FP16-shifted storage against an FP64 run of the same kernels
-    (the secondary reference; the FP64 oracle is too slow at this size):
-    D3Q19 TRT 256^3 TGV, 1000 steps, AA.  Relative L2 over all cells of
-    rho - 1 and of u, and the kinetic energy ratio E(T)/E(0)."""
+    (the secondary reference; the FP64 oracle is too slow at these sizes).
+    Relative L2 of rho - 1 and of u (fluid cells), kinetic energy ratios.
+    - D3Q19 TRT 256^3 TGV, 1000 steps, AA;
+    - D3Q19 MRT channel 512x128x128 (walls, inlet 0.05, outlet, obstacles),
+      2000 steps from rest, AA;
+    - D3Q27 cumulant 384^3 TGV u0 = 0.05: FP32 kinetic-energy decay over 5000
+      steps, and FP32 against FP64 after 100 steps (FP64 cumulant arithmetic
+      runs at about 0.5 GLUPS on this part, so 5000 FP64 steps would take
+      minutes)."""
     import torch
 
     from paper_2001_11806_gb300 import inputs
     from paper_2001_11806_gb300.sim import Sim
+
+    def run(kw, rho, u, T, storages, mask=None):
+        fields, ke = {}, {}
+        for st in storages:
+            sim = Sim(storage=st, device=device, **kw)
+            sim.init_equilibrium(rho.reshape(-1), u.reshape(sim.d, -1))
+            e0 = sim.reduce()[4]
+            sim.step(T)
+            ke[st] = sim.reduce()[4] / e0 if e0 > 0 else None
+            r, v = sim.macroscopic(True)
+            fields[st] = (r.cpu().numpy(), v.cpu().numpy())
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
+        return fields, ke
+
+    out = []
+    # D3Q19 TRT TGV
     n, T = N_SIDE, 1000
     rho, u = inputs.tgv3d(n, U0, NOISE, SEED)
-    fields, ke = {}, {}
-    for st in ["f64", "f32", "f16s"]:
-        sim = Sim("D3Q19", "trt", st, "aa", (n,) * 3, omega=[OMEGA_E], trt_magic=MAGIC, device=device)
-        sim.init_equilibrium(rho.reshape(-1), u.reshape(3, -1))
-        e0 = sim.reduce()[4]
-        sim.step(T)
-        ke[st] = sim.reduce()[4] / e0
-        r, v = sim.macroscopic(True)
-        fields[st] = (r.cpu().numpy(), v.cpu().numpy())
-        sim.close()
-        del sim
-        torch.cuda.empty_cache()
-    r64, u64 = fields["f64"]
-    out = {"workload": "D3Q19 TRT 256^3 TGV u0 = 0.02, 1000 steps, AA; reference: FP64 GPU run",
-           "ke_ratio_f64": round(float(ke["f64"]), 8)}
+    kw = dict(stencil="D3Q19", collision="trt", pattern="aa", shape=(n,) * 3, omega=[OMEGA_E], trt_magic=MAGIC)
+    fields, ke = run(kw, rho, u, T, ["f64", "f32", "f16s"])
+    entry = {"workload": "D3Q19 TRT 256^3 TGV u0 = 0.02, 1000 steps, AA; reference: FP64 GPU run",
+             "ke_ratio_f64": round(float(ke["f64"]), 8)}
     for st in ["f32", "f16s"]:
-        r, v = fields[st]
-        out[st] = {"rho_minus_1": float(np.linalg.norm(r - r64) / np.linalg.norm(r64 - 1.0)),
-                   "u": float(max(np.linalg.norm(v[a] - u64[a]) / np.linalg.norm(u64[a]) for a in range(3))),
-                   "ke_ratio": round(float(ke[st]), 8)}
+        entry[st] = dict(_rel_errors(fields[st], fields["f64"]), ke_ratio=round(float(ke[st]), 8))
+    out.append(entry)
+    # D3Q19 MRT channel
+    shape = (512, 128, 128)
+    flags = inputs.channel_flags(*shape)
+    fluid = flags.reshape(-1) == 0
+    N = flags.size
+    kw = dict(stencil="D3Q19", collision="mrt", pattern="aa", shape=shape, omega=[1.7, 1.0, 1.0, 1.0],
+              periodic=(False, False, False), u_wall=(0.05, 0.0, 0.0), flags=flags)
+    fields, _ = run(kw, np.ones(N), np.zeros((3, N)), 2000, ["f64", "f32", "f16s"])
+    entry = {"workload": "D3Q19 MRT channel 512x128x128, inlet 0.05, 2000 steps from rest, AA; fluid cells; "
+                         "reference: FP64 GPU run",
+             "mean_ux_f64": round(float(fields["f64"][1][0][fluid].mean()), 8)}
+    for st in ["f32", "f16s"]:
+        entry[st] = _rel_errors(fields[st], fields["f64"], fluid)
+    out.append(entry)
+    # D3Q27 cumulant TGV
+    n = 384
+    rho, u = inputs.tgv3d(n, 0.05, 0.0, SEED)
+    kw = dict(stencil="D3Q27", collision="cumulant", pattern="aa", shape=(n,) * 3, omega=[1.95, 1.0, 1.0])
+    sim = Sim(storage="f32", device=device, **kw)
+    sim.init_equilibrium(rho.reshape(-1), u.reshape(3, -1))
+    e0 = sim.reduce()[4]
+    decay = {}
+    for t in range(1000, 5001, 1000):
+        sim.step(1000)
+        decay[str(t)] = round(float(sim.reduce()[4] / e0), 6)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    fields, ke = run(kw, rho, u, 100, ["f64", "f32"])
+    out.append({"workload": "D3Q27 cumulant 384^3 TGV u0 = 0.05, omega 1.95, AA",
+                "ke_ratio_f32": decay,
+                "f32_vs_f64_after_100_steps": dict(_rel_errors(fields["f32"], fields["f64"]),
+                                                   ke_ratio_f64=round(float(ke["f64"]), 8),
+                                                   ke_ratio_f32=round(float(ke["f32"]), 8))})
     return out
 
 

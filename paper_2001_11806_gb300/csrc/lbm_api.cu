@@ -75,12 +75,26 @@ struct lbm_ctx {
   CollideParams cp;
   OpsTable ops;
   std::string err;
+  // Small domains: lbm_step replays kGraphSteps sweeps as one CUDA graph
+  // (recorded on a private stream; index = pull buffer holding P, 0 for the
+  // single-array patterns, which start a graph at even parity).
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  ~lbm_ctx() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace {
 
 const char* kStatusNames[] = {"LBM_OK", "LBM_E_INVAL", "LBM_E_UNSUPPORTED", "LBM_E_CUDA", "LBM_E_NOMEM",
                               "LBM_E_BUFSIZE", "LBM_E_NONFINITE", "LBM_E_BOUNDS", "LBM_E_STATE"};
+
+// CUDA graphs for small domains, where a sweep is shorter than its launch.
+constexpr int kGraphSteps = 32;
+constexpr long long kGraphMaxCells = 1 << 20;
 
 struct Layout {
   size_t mask_off, mask_bytes, list_off, count_off, part_off, res_off, total;
@@ -284,6 +298,50 @@ void set_interior(SweepArgs& a, const lbm_ctx* c, int kind) {
   }
 }
 
+// One time step from state (t, cur) enqueued on stream s.
+cudaError_t sweep_once(lbm_ctx* c, cudaStream_t s, int64_t t, int cur) {
+  if (c->p.pattern == LBM_PULL) {
+    SweepArgs a = make_args(c, c->buf[cur], c->buf[1 - cur]);
+    set_interior(a, c, K_PULL);
+    return c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, s);
+  }
+  SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
+  const bool odd = (t & 1) != 0;
+  const int kind = c->p.pattern == LBM_AA ? (odd ? K_AA_ODD : K_AA_EVEN) : (odd ? K_ESO_ODD : K_ESO_EVEN);
+  set_interior(a, c, kind);
+  return c->ops.sweep(c->kernel_op, kind, c->has_mask, a, s);
+}
+
+// Records kGraphSteps sweeps starting from pull buffer g (or even parity)
+// into c->graph[g].  kGraphSteps is even, so the graph ends in the state
+// layout it starts from.
+cudaError_t record_graph(lbm_ctx* c, int g) {
+  cudaError_t e = cudaSuccess;
+  if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = cudaSuccess;
+  int cur = g;
+  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) {
+    le = sweep_once(c, c->cap_stream, i, cur);
+    cur = 1 - cur;
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[g], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  return e;
+}
+
+void drop_graphs(lbm_ctx* c) {
+  for (auto& g : c->graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
 int current_view(const lbm_ctx* c) {
   if (c->p.pattern == LBM_PULL) return V_PULL;
   if (c->p.pattern == LBM_ESOTWIST) return (c->t & 1) ? V_ESO_ODD : V_ESO_EVEN;
@@ -453,22 +511,23 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* P) {
 
 lbm_status lbm_step(lbm_ctx* c, int32_t n) {
   if (!c || n < 0) return LBM_E_INVAL;
-  for (int32_t i = 0; i < n; ++i) {
-    cudaError_t e;
-    if (c->p.pattern == LBM_PULL) {
-      SweepArgs a = make_args(c, c->buf[c->cur], c->buf[1 - c->cur]);
-      set_interior(a, c, K_PULL);
-      e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
-      if (e == cudaSuccess) c->cur = 1 - c->cur;
-    } else {
-      SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
-      const bool odd = (c->t & 1) != 0;
-      const int kind = c->p.pattern == LBM_AA ? (odd ? K_AA_ODD : K_AA_EVEN) : (odd ? K_ESO_ODD : K_ESO_EVEN);
-      set_interior(a, c, kind);
-      e = c->ops.sweep(c->kernel_op, kind, c->has_mask, a, c->stream);
+  const bool graphs = c->N <= kGraphMaxCells;
+  while (n > 0) {
+    const int g = c->p.pattern == LBM_PULL ? c->cur : 0;
+    const bool aligned = c->p.pattern == LBM_PULL || (c->t & 1) == 0;
+    if (graphs && aligned && n >= kGraphSteps) {
+      cudaError_t e = c->graph[g] ? cudaSuccess : record_graph(c, g);
+      if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[g], c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "step graph");
+      c->t += kGraphSteps;
+      n -= kGraphSteps;
+      continue;
     }
+    const cudaError_t e = sweep_once(c, c->stream, c->t, c->cur);
     if (e != cudaSuccess) return cuda_fail(c, e, "step");
+    if (c->p.pattern == LBM_PULL) c->cur = 1 - c->cur;
     ++c->t;
+    --n;
   }
   return LBM_OK;
 }
@@ -548,6 +607,7 @@ lbm_status lbm_set_force(lbm_ctx* c, const double F[3]) {
     return LBM_E_UNSUPPORTED;
   for (int i = 0; i < 3; ++i) c->p.force[i] = F[i];
   fill_collide_params(c);
+  drop_graphs(c);  // recorded sweeps carry the old force
   return LBM_OK;
 }
 

@@ -378,3 +378,33 @@ def test_esotwist_channel_with_open_first_layer(stencil, collision):
                  u_wall=(0.05, 0.0, 0.0))
     ef, er, eu = _errs(r)
     assert ef < 1e-12 and er < 1e-12 and eu < 1e-12, (ef, er, eu)
+
+
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
+def test_replayed_steps_match_single_steps(pattern):
+    """Small domains replay 32-step CUDA graphs inside lbm_step(n); the bits
+    must equal n single steps, from either pull buffer or AA parity, and a
+    force change must reach the replayed steps."""
+    from paper_2001_11806_gb300 import _lib
+    import ctypes
+    lat = olat.d3q19()
+    shape = (12, 10, 8)
+    fl = _flags(shape)
+    P = inputs.random_pdfs(lat.w, shape[::-1], seed=14).reshape(19, -1)
+    out = []
+    for chunks in ([1] * 75, [3, 70, 2], [75]):
+        sim = Sim("D3Q19", "trt", "f32", pattern, shape, periodic=(False, False, True), omega=[1.6, 1.1],
+                  u_wall=(0.04, 0.0, 0.0), flags=fl, force=(1e-5, 0.0, 0.0))
+        sim.set_state(P)
+        for i, k in enumerate(chunks):
+            sim.step(k)
+        F = (ctypes.c_double * 3)(2e-5, -1e-5, 0.0)
+        _lib.check(_lib.lib().lbm_set_force(sim.ctx, F), sim.ctx, "set_force")
+        for k in chunks:
+            sim.step(k)
+        assert sim.t == 150
+        out.append(sim.populations().cpu().numpy())
+        sim.close()
+    fluid = fl.reshape(-1) == 0
+    assert np.array_equal(out[0][:, fluid], out[1][:, fluid])
+    assert np.array_equal(out[0][:, fluid], out[2][:, fluid])

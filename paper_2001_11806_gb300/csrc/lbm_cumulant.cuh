@@ -37,26 +37,38 @@ __host__ __device__ constexpr int slot27(int q) {
   return 9 * (D3Q27::cx(q) + 1) + 3 * (D3Q27::cy(q) + 1) + (D3Q27::cz(q) + 1);
 }
 
+// With t = f(+1) - f(-1) and S = f(+1) + f(-1) of a line:
+//   m0 = S + f(0),  m1 = t - u m0,  m2 = S - 2 u t + u^2 m0 = S - u (t + m1),
+// and back: t = m1 + u m0, S = m2 + u (m1 + t), f(0) = m0 - S,
+// f(+-1) = (S +- t) / 2.
 template <class T>
 __device__ __forceinline__ void chimera_fwd(T& a, T& b, T& c, T u) {
-  const T m0 = a + b + c;
-  const T k1 = c - a;
-  const T k2 = c + a;
+  const T S = c + a, t = c - a;
+  const T m0 = S + b;
+  const T m1 = fma(-u, m0, t);
   a = m0;
-  b = k1 - u * m0;
-  c = k2 - T(2) * u * k1 + u * u * m0;
+  b = m1;
+  c = fma(-u, t + m1, S);
+}
+
+// the central part of chimera_fwd for a line already holding (m0, t, S)
+template <class T>
+__device__ __forceinline__ void chimera_shift(T& b, T& c, T m0, T u) {
+  const T t = b;
+  const T m1 = fma(-u, m0, t);
+  b = m1;
+  c = fma(-u, t + m1, c);
 }
 
 template <class T>
 __device__ __forceinline__ void chimera_bwd(T& a, T& b, T& c, T u) {
   const T m0 = a, m1 = b, m2 = c;
-  const T uu = u * u;
-  const T f0 = m0 * (T(1) - uu) - T(2) * u * m1 - m2;
-  const T fp = T(0.5) * (m0 * (uu + u) + m1 * (T(2) * u + T(1)) + m2);
-  const T fm = T(0.5) * (m0 * (uu - u) + m1 * (T(2) * u - T(1)) + m2);
-  a = fm;
-  b = f0;
-  c = fp;
+  const T t = fma(u, m0, m1);
+  const T S = fma(u, m1 + t, m2);
+  const T ht = T(0.5) * t;
+  a = fma(T(0.5), S, -ht);
+  b = m0 - S;
+  c = fma(T(0.5), S, ht);
 }
 
 #define LBM_C(a, b, c) F[9 * (a) + 3 * (b) + (c)]
@@ -75,23 +87,35 @@ __device__ __forceinline__ void chimera_bwd(T& a, T& b, T& c, T u) {
 // transformed back, which yields h* = f* - w directly.
 template <class T>
 __device__ __forceinline__ void collide_cumulant(T (&h)[27], const CollideParams& p) {
+  T F[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) F[slot27(q)] = h[q];
+  // z lines first as raw sums (m0, t, S); rho and j follow from them: line i
+  // has c_x = i / 3 - 1, c_y = i % 3 - 1
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T a = F[3 * i], b = F[3 * i + 1], c = F[3 * i + 2];
+    const T S = c + a;
+    F[3 * i] = S + b;
+    F[3 * i + 1] = c - a;
+    F[3 * i + 2] = S;
+  }
   T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    drho += h[q];
-    jx += T(D3Q27::cx(q)) * h[q];
-    jy += T(D3Q27::cy(q)) * h[q];
-    jz += T(D3Q27::cz(q)) * h[q];
+  for (int i = 0; i < 9; ++i) {
+    drho += F[3 * i];
+    jz += F[3 * i + 1];
+    if (i / 3 == 2) jx += F[3 * i];
+    if (i / 3 == 0) jx -= F[3 * i];
+    if (i % 3 == 2) jy += F[3 * i];
+    if (i % 3 == 0) jy -= F[3 * i];
   }
   const T rho = T(1) + drho;
   const T inv = T(1) / rho;
   const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  T F[27];
+  // forward transform of h: z lines (central part), y lines, x lines
 #pragma unroll
-  for (int q = 0; q < 27; ++q) F[slot27(q)] = h[q];
-  // forward transform of h: z lines, y lines, x lines
-#pragma unroll
-  for (int i = 0; i < 9; ++i) chimera_fwd(F[3 * i], F[3 * i + 1], F[3 * i + 2], uz);
+  for (int i = 0; i < 9; ++i) chimera_shift(F[3 * i + 1], F[3 * i + 2], F[3 * i], uz);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll

@@ -86,18 +86,28 @@ __device__ __forceinline__ void relax_transpose(const T (&lam)[L::Q], T (&nu)[L:
   }
 }
 
-// mu = C'(h)^T lambda and this cell's body-force gradient dpsi/dF.
+// nu_q = (R^T lambda)_q for SRT/TRT, from the pair (lambda_q, lambda_qbar);
+// recomputed where needed instead of held in registers
 template <class L, class T, int OP>
-__device__ __forceinline__ void collide_vjp(const T (&h)[L::Q], const T (&lam)[L::Q], const CollideParams& p,
-                                            T (&mu)[L::Q], T (&gF)[3]) {
-  T drho = T(0), J[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    drho += h[q];
-    J[0] += T(L::cx(q)) * h[q];
-    J[1] += T(L::cy(q)) * h[q];
-    J[2] += T(L::cz(q)) * h[q];
-  }
+__device__ __forceinline__ T nu_pair(const T (&lam)[L::Q], int q, const CollideParams& p) {
+  const T oe = rate<T>(p, 0);
+  const T oo = OP == OP_SRT ? oe : rate<T>(p, 1);
+  if (q == 0) return oe * lam[0];
+  const int qb = opp(q);
+  const T lp = T(0.5) * (lam[q] + lam[qb]);
+  const T lm = T(0.5) * (lam[q] - lam[qb]);
+  return oe * lp + oo * lm;
+}
+
+// The scalar a, vector b and body-force gradient of
+//   mu = C'(h)^T lambda = lambda - nu + a 1 + C b
+// for the cell whose streamed populations have moments drho = sum h and
+// j = sum c h (before the Guo half force); nu is returned for MRT only (SRT
+// and TRT recompute it with nu_pair).
+template <class L, class T, int OP>
+__device__ __forceinline__ void collide_vjp(T drho, const T (&jh)[3], const T (&lam)[L::Q], const CollideParams& p,
+                                            T (&nu)[L::Q], T& a_out, T (&b)[3], T (&gF)[3]) {
+  T J[3] = {jh[0], jh[1], jh[2]};
   const bool force = p.has_force != 0;
   T F[3] = {T(0), T(0), T(0)};
   if (force) {
@@ -107,14 +117,14 @@ __device__ __forceinline__ void collide_vjp(const T (&h)[L::Q], const T (&lam)[L
   const bool comp = p.incompressible == 0;
   const T rho = T(1) + drho;
   const T inv0 = comp ? T(1) / rho : T(1);
-  T nu[L::Q];
-  relax_transpose<L, T, OP>(lam, nu, p);
+  if constexpr (OP == OP_MRT) relax_transpose<L, T, OP>(lam, nu, p);
   T n0 = T(0), n1[3] = {T(0), T(0), T(0)}, k0 = T(0), k1[3] = {T(0), T(0), T(0)};
   Sym3<T> N2, K2;
 #pragma unroll
   for (int q = 0; q < L::Q; ++q) {
-    wmoments<L, T>(q, nu[q], n0, n1, N2);
-    if (force) wmoments<L, T>(q, lam[q] - T(0.5) * nu[q], k0, k1, K2);
+    const T nq = OP == OP_MRT ? nu[q] : nu_pair<L, T, OP>(lam, q, p);
+    wmoments<L, T>(q, nq, n0, n1, N2);
+    if (force) wmoments<L, T>(q, lam[q] - T(0.5) * nq, k0, k1, K2);
   }
   T N2J[3];
   sym_mul(N2, J, N2J);
@@ -122,7 +132,6 @@ __device__ __forceinline__ void collide_vjp(const T (&h)[L::Q], const T (&lam)[L
   const T JN2J = J[0] * N2J[0] + J[1] * N2J[1] + J[2] * N2J[2];
   T a = n0;
   if (comp) a -= inv0 * inv0 * (T(4.5) * JN2J - T(1.5) * n0 * JJ);
-  T b[3];
   for (int d = 0; d < 3; ++d) b[d] = T(3) * n1[d] + inv0 * (T(9) * N2J[d] - T(3) * n0 * J[d]);
   gF[0] = gF[1] = gF[2] = T(0);
   if (force) {
@@ -136,9 +145,7 @@ __device__ __forceinline__ void collide_vjp(const T (&h)[L::Q], const T (&lam)[L
     for (int d = 0; d < 3; ++d) gF[d] = T(0.5) * b[d] + T(3) * k1[d] + inv0 * (T(9) * K2J[d] - T(3) * k0 * J[d]);
   }
   if (L::D == 2) { b[2] = T(0); gF[2] = T(0); }
-#pragma unroll
-  for (int q = 0; q < L::Q; ++q)
-    mu[q] = lam[q] - nu[q] + a + T(L::cx(q)) * b[0] + T(L::cy(q)) * b[1] + T(L::cz(q)) * b[2];
+  a_out = a;
 }
 
 template <class T>
@@ -157,7 +164,6 @@ template <class L, class ST, bool BND>
 __device__ __forceinline__ void pull_h(const SweepArgs& a, const Nbr& nb, int cell, uint32_t mask,
                                        typename ST::T (&h)[L::Q]) {
   using S = typename ST::S;
-  using T = typename ST::T;
 #pragma unroll
   for (int q = 0; q < L::Q; ++q) {
     const bool b = BND && ((mask >> q) & 1u);
@@ -195,10 +201,29 @@ __device__ __forceinline__ void scatter_T(const SweepArgs& a, const Nbr& nb, int
   }
 }
 
+// A global load the compiler may not merge with an earlier load of the same
+// address (asm volatile), so the earlier value need not stay in a register.
+__device__ __forceinline__ float reload(const float* p) {
+  float v;
+  asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double reload(const double* p) {
+  double v;
+  asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+// The adjoint sweep.  The forward populations f(y) = S(P_prev)(y) enter only
+// through rho and j, so they are summed while loaded and not kept.  Periodic
+// domains use the same pre-shifted stream bases as the forward pull sweep in
+// rows whose y/z neighbours do not wrap: SweepArgs::srci for P_prev and
+// SweepArgs::dsti for lambda_out (base of stream q minus the offset of c_q).
 template <class L, class ST, int OP, bool BND>
 __global__ void __launch_bounds__(kBlockX) k_adjoint(const SweepArgs a, const typename ST::T* lam_in,
                                                      typename ST::T* lam_out, double* dLdF) {
   using T = typename ST::T;
+  using S = typename ST::S;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   T gF[3] = {T(0), T(0), T(0)};
   if (x < a.g.nx) {
@@ -210,14 +235,71 @@ __global__ void __launch_bounds__(kBlockX) k_adjoint(const SweepArgs a, const ty
     if (mask & MASK_SOLID) {
       for (int q = 0; q < L::Q; ++q) lam_out[q * N + cell] = T(0);
     } else {
-      const Nbr nb = make_nbr(a.g, x, y, z);
-      T h[L::Q], lam[L::Q], mu[L::Q];
-      pull_h<L, ST, BND>(a, nb, cell, mask, h);
-      inlet_fix<L, T, BND>(a, x, y, z, mask, h);
+      bool fast = false;
+      if constexpr (!BND) fast = row_inner<L>(a.g, y, z);
+      const int im = cell + (x == 0 ? a.g.nx : 0);
+      const int ip = cell - (x == a.g.nx - 1 ? a.g.nx : 0);
+      T drho = T(0), jh[3] = {T(0), T(0), T(0)};
+      if (fast) {
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) {
+          const int idx = L::cx(q) > 0 ? im : (L::cx(q) < 0 ? ip : cell);
+          const T hq = ST::to_h(reinterpret_cast<const S*>(a.srci[q])[idx], L::w(q));
+          drho += hq;
+          jh[0] += T(L::cx(q)) * hq; jh[1] += T(L::cy(q)) * hq; jh[2] += T(L::cz(q)) * hq;
+        }
+      } else {
+        const Nbr nb = make_nbr(a.g, x, y, z);
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) {
+          const bool b = BND && ((mask >> q) & 1u);
+          const int qs = b ? opp(q) : q;
+          const int idx = b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+          const T hq = ST::to_h(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
+          drho += hq;
+          jh[0] += T(L::cx(q)) * hq; jh[1] += T(L::cy(q)) * hq; jh[2] += T(L::cz(q)) * hq;
+        }
+        if constexpr (BND) {
+          // inlet links carry the UBB constant (no outlet links here)
+          if (mask & MASK_SPECIAL) {
+            for (int q = 1; q < L::Q; ++q) {
+              if ((mask >> q) & 1u) {
+                if (LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q)) == L_INLET) {
+                  const T u = ubb_term<L, T>(q, a.cp);
+                  drho += u;
+                  jh[0] += T(L::cx(q)) * u; jh[1] += T(L::cy(q)) * u; jh[2] += T(L::cz(q)) * u;
+                }
+              }
+            }
+          }
+        }
+      }
+      T lam[L::Q], nu[L::Q];
 #pragma unroll
       for (int q = 0; q < L::Q; ++q) lam[q] = lam_in[q * N + cell];
-      collide_vjp<L, T, OP>(h, lam, a.cp, mu, gF);
-      scatter_T<L, T, BND>(a, nb, cell, mask, mu, lam_out);
+      T av, bv[3];
+      collide_vjp<L, T, OP>(drho, jh, lam, a.cp, nu, av, bv, gF);
+      // scatter mu(y) through the transposed streaming map; SRT/TRT read
+      // lambda again (a cache hit) instead of holding it across the moments
+      if constexpr (OP != OP_MRT) {
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) lam[q] = reload(lam_in + q * N + cell);
+      }
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) {
+        const T nq = OP == OP_MRT ? nu[q] : nu_pair<L, T, OP>(lam, q, a.cp);
+        const T mu = lam[q] - nq + av + T(L::cx(q)) * bv[0] + T(L::cy(q)) * bv[1] + T(L::cz(q)) * bv[2];
+        if (fast) {
+          const int idx = L::cx(q) > 0 ? im : (L::cx(q) < 0 ? ip : cell);
+          reinterpret_cast<T*>(a.dsti[q])[idx] = mu;
+        } else {
+          const Nbr nb = make_nbr(a.g, x, y, z);
+          const bool b = BND && ((mask >> q) & 1u);
+          const int qd = b ? opp(q) : q;
+          const int idx = b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+          lam_out[qd * N + idx] = mu;
+        }
+      }
     }
   }
   if (dLdF != nullptr && a.cp.has_force) block_add3(gF, dLdF);

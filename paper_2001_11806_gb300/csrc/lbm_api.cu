@@ -647,6 +647,19 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const void* P_prev, const void* lam_in, 
   lbm_status st = adjoint_ok(c);
   if (st != LBM_OK) return st;
   SweepArgs a = make_args(c, P_prev, nullptr);
+  set_interior(a, c, K_PULL);
+  // lambda_out bases for the scatter of the periodic fast path: stream q
+  // shifted by -c_q (adjoint arrays are FP64 for LBM_F64, FP32 otherwise)
+  {
+    int32_t cv[27 * 3];
+    lbm_stencil_info(c->p.stencil, nullptr, nullptr, cv, nullptr);
+    const long long nx = c->p.nx, nxy = (long long)c->p.nx * c->p.ny;
+    const long long el = c->p.storage == LBM_F64 ? 8 : 4;
+    for (int q = 0; q < c->q; ++q) {
+      const long long off = cv[3 * q] + nx * cv[3 * q + 1] + nxy * cv[3 * q + 2];
+      a.dsti[q] = reinterpret_cast<char*>(reinterpret_cast<uintptr_t>(lam_out) + (q * c->N - off) * el);
+    }
+  }
   cudaError_t e = c->ops.adjoint(c->p.collision, c->has_mask, a, lam_in, lam_out, dLdF, c->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "adjoint_step");
 }

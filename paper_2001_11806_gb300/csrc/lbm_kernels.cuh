@@ -648,14 +648,21 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
   // x of the neighbours of cell 0 (x0) and cell 1 (x0 + 1) for dx = -1, 0, 1
   const int xa[3] = {x0 == 0 ? nx - 1 : x0 - 1, x0, x0 + 1};
   const int xb[3] = {x0, x0 + 1, x0 + 2 == nx ? 0 : x0 + 2};
+  constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
   __half2 P[L::Q];
 #pragma unroll
   for (int q = 0; q < L::Q; ++q) {
-    // pull / AA even read direction q; AA odd reads slot qbar
-    const int qs = KIND == K_AA_ODD ? opp(q) : q;
+    // pull / AA even / esoteric twist even read slot q; AA odd and esoteric
+    // twist odd read slot qbar
+    const int qs = (KIND == K_AA_ODD || KIND == K_ESO_ODD) ? opp(q) : q;
     const __half* base = reinterpret_cast<const __half*>(a.srcq[qs]);
     if constexpr (KIND == K_AA_EVEN) {
       P[q] = *reinterpret_cast<const __half2*>(base + cell);
+    } else if constexpr (ESO) {
+      // location x + max(-c_q, 0): x0 and x0 + 1, or x0 + 1 and x0 + 2
+      const int row = yo[eso_rd(L::cy(q)) + 1] + zo[eso_rd(L::cz(q)) + 1];
+      if (eso_rd(L::cx(q)) == 0) P[q] = *reinterpret_cast<const __half2*>(base + row + x0);
+      else P[q] = __halves2half2(base[row + xb[1]], base[row + xb[2]]);
     } else {
       const int dx = -L::cx(q), dy = -L::cy(q), dz = -L::cz(q);
       const int row = yo[dy + 1] + zo[dz + 1];
@@ -682,6 +689,25 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q)
       *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.dstq[opp(q)]) + cell) = P[q];
+  } else if constexpr (ESO) {
+    int tx;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+    const int x1 = 2 * (blockIdx.x * blockDim.x + tx);
+    const int yo2[3] = {(y == 0 ? a.g.ny - 1 : y - 1) * sy, y * sy, (y == a.g.ny - 1 ? 0 : y + 1) * sy};
+    const int zo2[3] = {(z == 0 ? a.g.nz - 1 : z - 1) * sz, z * sz, (z == a.g.nz - 1 ? 0 : z + 1) * sz};
+    const int xb1 = x1 + 1, xb2 = x1 + 2 == nx ? 0 : x1 + 2;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+      // slot qbar (even) or q (odd) at x + max(c_q, 0)
+      __half* base = reinterpret_cast<__half*>(a.dstq[KIND == K_ESO_EVEN ? opp(q) : q]);
+      const int row = yo2[eso_wr(L::cy(q)) + 1] + zo2[eso_wr(L::cz(q)) + 1];
+      if (eso_wr(L::cx(q)) == 0) {
+        *reinterpret_cast<__half2*>(base + row + x1) = P[q];
+      } else {
+        base[row + xb1] = __low2half(P[q]);
+        base[row + xb2] = __high2half(P[q]);
+      }
+    }
   } else {
     // rebuild the neighbour offsets from a fresh %tid.x read (see k_sweep)
     int tx;
@@ -1065,7 +1091,7 @@ inline dim3 sweep_grid(const Geom& g) {
 
 template <class L, class ST, int OP, int KIND>
 cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
-  if constexpr (ST::ID == StF16S::ID && KIND <= K_AA_ODD) {
+  if constexpr (ST::ID == StF16S::ID) {
     if (!bnd && (a.g.nx % 2) == 0) {
       Geom half = a.g;
       half.nx = a.g.nx / 2;

@@ -103,16 +103,33 @@ def test_config2_d3q19_trt_f32_aa_256():
     m = oco.Method(lat, "trt", [1.8, oco.trt_odd_rate(1.8, 3 / 16)])
     cells = _sample_cells((n, n, n), 24, 11) + [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 7)]
     _check(sim, m, (n, n, n), rho0, u0, steps, cells)
-    # the two-grid pull sweep of the same workload
-    sim2 = Sim("D3Q19", "trt", "f32", "pull", (n, n, n), omega=[1.8], trt_magic=3 / 16)
-    sim2.init_equilibrium(rho0.reshape(-1), u0.reshape(3, -1))
-    sim2.step(steps)
-    _check(sim2, m, (n, n, n), rho0, u0, steps, cells[:8])
+    # the two-grid pull sweep and the esoteric twist on the same workload
+    for pattern in ["pull", "eso"]:
+        sim2 = Sim("D3Q19", "trt", "f32", pattern, (n, n, n), omega=[1.8], trt_magic=3 / 16)
+        sim2.init_equilibrium(rho0.reshape(-1), u0.reshape(3, -1))
+        sim2.step(steps)
+        _check(sim2, m, (n, n, n), rho0, u0, steps, cells[:8])
+        del sim2
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("stencil", ["D3Q19", "D3Q27"])
+def test_kbc_256_benchmark_variant(stencil):
+    """The KBC variants of the benchmark: 256^3 TGV, omega_s = omega_b = 1.95, AA."""
+    n, steps = 256, 3
+    rho0, u0 = inputs.tgv3d(n, 0.02, 1e-4, 42)
+    sim = Sim(stencil, "kbc", "f32", "aa", (n, n, n), omega=[1.95, 1.95])
+    sim.init_equilibrium(rho0.reshape(-1), u0.reshape(3, -1))
+    sim.step(steps)
+    m = oco.Method(olat.get(stencil), "kbc", [1.95, 1.95])
+    cells = _sample_cells((n, n, n), 6, 17) + [(0, 0, 0), (n - 1, n - 1, n - 1)]
+    _check(sim, m, (n, n, n), rho0, u0, steps, cells)
 
 
 def test_config3_d3q19_mrt_channel_512x128x128():
     """D3Q19 MRT channel: walls, UBB inlet 0.05, outlet, random spheres
-    (porosity 0.8); FP32 and FP16-shifted storage, pull pattern."""
+    (porosity 0.8); FP32 (pull and AA) and FP16-shifted (AA) storage, the
+    patterns of the benchmark's channel variants."""
     shape = (512, 128, 128)
     steps = 3
     flags = inputs.channel_flags(*shape)
@@ -124,8 +141,8 @@ def test_config3_d3q19_mrt_channel_512x128x128():
     cells = _sample_cells(shape, 24, 5, fluid)
     # cells next to the inlet, the outlet and a wall
     cells += [(1, 64, 64), (510, 64, 64), (200, 1, 1)]
-    for storage, tol in [("f32", 1e-5), ("f16s", 5e-3)]:
-        sim = Sim("D3Q19", "mrt", storage, "pull", shape, periodic=per, omega=[1.7, 1.0, 1.0, 1.0],
+    for storage, pattern, tol in [("f32", "pull", 1e-5), ("f32", "aa", 1e-5), ("f16s", "aa", 5e-3)]:
+        sim = Sim("D3Q19", "mrt", storage, pattern, shape, periodic=per, omega=[1.7, 1.0, 1.0, 1.0],
                   u_wall=(0.05, 0.0, 0.0), flags=flags)
         sim.init_equilibrium(rho0.reshape(-1), u0.reshape(3, -1))
         sim.step(steps)

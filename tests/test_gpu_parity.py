@@ -269,7 +269,7 @@ def test_poiseuille_exact_on_gpu():
 
 @pytest.mark.parametrize("stencil,collision", [("D2Q9", "trt"), ("D3Q19", "trt"), ("D3Q19", "mrt"),
                                                ("D3Q27", "srt"), ("D3Q27", "cumulant"), ("D3Q19", "kbc")])
-@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
 @pytest.mark.parametrize("nx", [534, 151])
 def test_f16_two_cell_kernel_parity(stencil, collision, pattern, nx):
     """Periodic FP16-shifted runs with even nx use the two-cells-per-thread

@@ -229,7 +229,7 @@ def run_variants(device, peak):
 
     from paper_2001_11806_gb300 import inputs
     from paper_2001_11806_gb300.sim import Sim
-    elem = {"f64": 8, "f32": 4, "f16s": 2}
+    elem = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2}
     out = []
     specs = [
         ("D3Q19 TRT FP32 256^3 two-grid pull", dict(stencil="D3Q19", collision="trt", storage="f32", pattern="pull",
@@ -262,6 +262,9 @@ def run_variants(device, peak):
          "channel", 300),
         ("D3Q27 cumulant FP32 384^3 AA", dict(stencil="D3Q27", collision="cumulant", storage="f32", pattern="aa",
                                               shape=(384,) * 3, omega=[1.95, 1.0, 1.0]), "tgv", 100),
+        ("D3Q27 cumulant FP32-shifted 384^3 AA", dict(stencil="D3Q27", collision="cumulant", storage="f32s",
+                                                      pattern="aa", shape=(384,) * 3, omega=[1.95, 1.0, 1.0]),
+         "tgv", 100),
         ("D2Q9 SRT FP64 64^2 pull", dict(stencil="D2Q9", collision="srt", storage="f64", pattern="pull",
                                          shape=(64, 64, 1), omega=[1.6]), "tgv2d", 2000),
     ]

@@ -133,63 +133,74 @@ __device__ __forceinline__ void collide_cumulant(T (&h)[27], const CollideParams
   const T C110 = (LBM_C(1, 1, 0) + ux * uy) * inv;
   const T C101 = (LBM_C(1, 0, 1) + ux * uz) * inv;
   const T C011 = (LBM_C(0, 1, 1) + uy * uz) * inv;
-  const T C210 = (LBM_C(2, 1, 0) - m2x * uy) * inv, C201 = (LBM_C(2, 0, 1) - m2x * uz) * inv;
-  const T C120 = (LBM_C(1, 2, 0) - m2y * ux) * inv, C021 = (LBM_C(0, 2, 1) - m2y * uz) * inv;
-  const T C102 = (LBM_C(1, 0, 2) - m2z * ux) * inv, C012 = (LBM_C(0, 1, 2) - m2z * uy) * inv;
-  const T C111 = (LBM_C(1, 1, 1) - ux * uy * uz) * inv;
-  const T E220 = (LBM_C(2, 2, 0) + (x2 + y2) * third + x2 * y2 - drho * ninth) * inv;
-  const T E202 = (LBM_C(2, 0, 2) + (x2 + z2) * third + x2 * z2 - drho * ninth) * inv;
-  const T E022 = (LBM_C(0, 2, 2) + (y2 + z2) * third + y2 * z2 - drho * ninth) * inv;
-  const T C211 = (LBM_C(2, 1, 1) + m2x * uy * uz) * inv;
-  const T C121 = (LBM_C(1, 2, 1) + m2y * ux * uz) * inv;
-  const T C112 = (LBM_C(1, 1, 2) + m2z * ux * uy) * inv;
-  const T C221 = (LBM_C(2, 2, 1) - m2x * m2y * uz) * inv;
-  const T C212 = (LBM_C(2, 1, 2) - m2x * m2z * uy) * inv;
-  const T C122 = (LBM_C(1, 2, 2) - m2y * m2z * ux) * inv;
-  const T E222 = (LBM_C(2, 2, 2) + usq * ninth + (x2 * y2 + y2 * z2 + z2 * x2) * third + x2 * y2 * z2 -
-                  drho * T(1.0 / 27.0)) * inv;
-  // pre-collision cumulants of order 4-6 (the relations of the header with
-  // C200 = 1/3 + a, C220 = 1/9 + E220, C222 = 1/27 + E222, ...)
-  const T k220 = E220 - (a + b) * third - a * b - two * C110 * C110;
-  const T k202 = E202 - (a + c) * third - a * c - two * C101 * C101;
-  const T k022 = E022 - (b + c) * third - b * c - two * C011 * C011;
-  const T k211 = C211 - (third + a) * C011 - two * C110 * C101;
-  const T k121 = C121 - (third + b) * C101 - two * C110 * C011;
-  const T k112 = C112 - (third + c) * C110 - two * C101 * C011;
-  const T k221 = C221 - (third + a) * C021 - (third + b) * C201 - four * C110 * C111 - two * C101 * C120 -
-                 two * C011 * C210;
-  const T k212 = C212 - (third + a) * C012 - (third + c) * C210 - four * C101 * C111 - two * C110 * C102 -
-                 two * C011 * C201;
-  const T k122 = C122 - (third + b) * C102 - (third + c) * C120 - four * C011 * C111 - two * C110 * C012 -
-                 two * C101 * C021;
-  const T k222 = E222 - (E220 + E202 + E022) * third + (a + b + c) * ninth - (a * E022 + b * E202 + c * E220) +
-                 T(2.0 / 3.0) * (a * b + b * c + c * a) + two * a * b * c -
-                 four * (C110 * C112 + C101 * C121 + C011 * C211) -
-                 two * (C210 * C012 + C201 * C021 + C120 * C102) - four * C111 * C111 +
-                 T(16) * C110 * C101 * C011 +
-                 four * ((third + a) * C011 * C011 + (third + b) * C101 * C101 + (third + c) * C110 * C110);
-  // relaxation: shear (off-diagonals and diagonal differences), bulk (trace
-  // toward 3 c_s^2, i.e. a + b + c toward 0), higher orders toward 0
   const T om = rate<T>(p, 0), omb = rate<T>(p, 1), omh = rate<T>(p, 2);
   const T rs = T(1) - om, rh = T(1) - omh;
+  // Orders >= 3 enter the post-collision state only as rh * (pre-collision
+  // moment or cumulant); with omega_higher = 1 (rh = 0, a uniform branch)
+  // they are not formed at all.  r... = rh * k... below.
+  T P210 = T(0), P201 = T(0), P120 = T(0), P021 = T(0), P102 = T(0), P012 = T(0), P111 = T(0);
+  T r220 = T(0), r202 = T(0), r022 = T(0), r211 = T(0), r121 = T(0), r112 = T(0);
+  T r221 = T(0), r212 = T(0), r122 = T(0), r222 = T(0);
+  if (rh != T(0)) {
+    const T C210 = (LBM_C(2, 1, 0) - m2x * uy) * inv, C201 = (LBM_C(2, 0, 1) - m2x * uz) * inv;
+    const T C120 = (LBM_C(1, 2, 0) - m2y * ux) * inv, C021 = (LBM_C(0, 2, 1) - m2y * uz) * inv;
+    const T C102 = (LBM_C(1, 0, 2) - m2z * ux) * inv, C012 = (LBM_C(0, 1, 2) - m2z * uy) * inv;
+    const T C111 = (LBM_C(1, 1, 1) - ux * uy * uz) * inv;
+    const T E220 = (LBM_C(2, 2, 0) + (x2 + y2) * third + x2 * y2 - drho * ninth) * inv;
+    const T E202 = (LBM_C(2, 0, 2) + (x2 + z2) * third + x2 * z2 - drho * ninth) * inv;
+    const T E022 = (LBM_C(0, 2, 2) + (y2 + z2) * third + y2 * z2 - drho * ninth) * inv;
+    const T C211 = (LBM_C(2, 1, 1) + m2x * uy * uz) * inv;
+    const T C121 = (LBM_C(1, 2, 1) + m2y * ux * uz) * inv;
+    const T C112 = (LBM_C(1, 1, 2) + m2z * ux * uy) * inv;
+    const T C221 = (LBM_C(2, 2, 1) - m2x * m2y * uz) * inv;
+    const T C212 = (LBM_C(2, 1, 2) - m2x * m2z * uy) * inv;
+    const T C122 = (LBM_C(1, 2, 2) - m2y * m2z * ux) * inv;
+    const T E222 = (LBM_C(2, 2, 2) + usq * ninth + (x2 * y2 + y2 * z2 + z2 * x2) * third + x2 * y2 * z2 -
+                    drho * T(1.0 / 27.0)) * inv;
+    // pre-collision cumulants of order 4-6 (the relations of the header with
+    // C200 = 1/3 + a, C220 = 1/9 + E220, C222 = 1/27 + E222, ...)
+    const T k220 = E220 - (a + b) * third - a * b - two * C110 * C110;
+    const T k202 = E202 - (a + c) * third - a * c - two * C101 * C101;
+    const T k022 = E022 - (b + c) * third - b * c - two * C011 * C011;
+    const T k211 = C211 - (third + a) * C011 - two * C110 * C101;
+    const T k121 = C121 - (third + b) * C101 - two * C110 * C011;
+    const T k112 = C112 - (third + c) * C110 - two * C101 * C011;
+    const T k221 = C221 - (third + a) * C021 - (third + b) * C201 - four * C110 * C111 - two * C101 * C120 -
+                   two * C011 * C210;
+    const T k212 = C212 - (third + a) * C012 - (third + c) * C210 - four * C101 * C111 - two * C110 * C102 -
+                   two * C011 * C201;
+    const T k122 = C122 - (third + b) * C102 - (third + c) * C120 - four * C011 * C111 - two * C110 * C012 -
+                   two * C101 * C021;
+    const T k222 = E222 - (E220 + E202 + E022) * third + (a + b + c) * ninth - (a * E022 + b * E202 + c * E220) +
+                   T(2.0 / 3.0) * (a * b + b * c + c * a) + two * a * b * c -
+                   four * (C110 * C112 + C101 * C121 + C011 * C211) -
+                   two * (C210 * C012 + C201 * C021 + C120 * C102) - four * C111 * C111 +
+                   T(16) * C110 * C101 * C011 +
+                   four * ((third + a) * C011 * C011 + (third + b) * C101 * C101 + (third + c) * C110 * C110);
+    P210 = rh * C210; P201 = rh * C201; P120 = rh * C120;
+    P021 = rh * C021; P102 = rh * C102; P012 = rh * C012; P111 = rh * C111;
+    r220 = rh * k220; r202 = rh * k202; r022 = rh * k022;
+    r211 = rh * k211; r121 = rh * k121; r112 = rh * k112;
+    r221 = rh * k221; r212 = rh * k212; r122 = rh * k122; r222 = rh * k222;
+  }
+  // relaxation: shear (off-diagonals and diagonal differences), bulk (trace
+  // toward 3 c_s^2, i.e. a + b + c toward 0), higher orders toward 0
   const T d1 = rs * (a - b), d2 = rs * (a - c), tm1 = (T(1) - omb) * (a + b + c);
   const T A = (tm1 + d1 + d2) * third, B = (tm1 - two * d1 + d2) * third, Cc = (tm1 + d1 - two * d2) * third;
   const T P110 = rs * C110, P101 = rs * C101, P011 = rs * C011;
-  const T P210 = rh * C210, P201 = rh * C201, P120 = rh * C120;
-  const T P021 = rh * C021, P102 = rh * C102, P012 = rh * C012, P111 = rh * C111;
-  const T Q220 = rh * k220 + (A + B) * third + A * B + two * P110 * P110;
-  const T Q202 = rh * k202 + (A + Cc) * third + A * Cc + two * P101 * P101;
-  const T Q022 = rh * k022 + (B + Cc) * third + B * Cc + two * P011 * P011;
-  const T P211 = rh * k211 + (third + A) * P011 + two * P110 * P101;
-  const T P121 = rh * k121 + (third + B) * P101 + two * P110 * P011;
-  const T P112 = rh * k112 + (third + Cc) * P110 + two * P101 * P011;
-  const T P221 = rh * k221 + (third + A) * P021 + (third + B) * P201 + four * P110 * P111 + two * P101 * P120 +
+  const T Q220 = r220 + (A + B) * third + A * B + two * P110 * P110;
+  const T Q202 = r202 + (A + Cc) * third + A * Cc + two * P101 * P101;
+  const T Q022 = r022 + (B + Cc) * third + B * Cc + two * P011 * P011;
+  const T P211 = r211 + (third + A) * P011 + two * P110 * P101;
+  const T P121 = r121 + (third + B) * P101 + two * P110 * P011;
+  const T P112 = r112 + (third + Cc) * P110 + two * P101 * P011;
+  const T P221 = r221 + (third + A) * P021 + (third + B) * P201 + four * P110 * P111 + two * P101 * P120 +
                  two * P011 * P210;
-  const T P212 = rh * k212 + (third + A) * P012 + (third + Cc) * P210 + four * P101 * P111 + two * P110 * P102 +
+  const T P212 = r212 + (third + A) * P012 + (third + Cc) * P210 + four * P101 * P111 + two * P110 * P102 +
                  two * P011 * P201;
-  const T P122 = rh * k122 + (third + B) * P102 + (third + Cc) * P120 + four * P011 * P111 + two * P110 * P012 +
+  const T P122 = r122 + (third + B) * P102 + (third + Cc) * P120 + four * P011 * P111 + two * P110 * P012 +
                  two * P101 * P021;
-  const T Q222 = rh * k222 + (Q220 + Q202 + Q022) * third - (A + B + Cc) * ninth +
+  const T Q222 = r222 + (Q220 + Q202 + Q022) * third - (A + B + Cc) * ninth +
                  (A * Q022 + B * Q202 + Cc * Q220) - T(2.0 / 3.0) * (A * B + B * Cc + Cc * A) - two * A * B * Cc +
                  four * (P110 * P112 + P101 * P121 + P011 * P211) +
                  two * (P210 * P012 + P201 * P021 + P120 * P102) + four * P111 * P111 -

@@ -408,3 +408,29 @@ def test_replayed_steps_match_single_steps(pattern):
     fluid = fl.reshape(-1) == 0
     assert np.array_equal(out[0][:, fluid], out[1][:, fluid])
     assert np.array_equal(out[0][:, fluid], out[2][:, fluid])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f32s"])
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+def test_cumulant_with_higher_order_rate_not_one(storage, pattern):
+    """The cumulant sweep skips the pre-collision orders >= 3 when
+    omega_higher = 1; this covers the general branch (omega_higher = 1.4,
+    bulk rate 1.2) on walls, an inlet and an outlet."""
+    lat = olat.d3q27()
+    shape = _shape("D3Q27")
+    fl = _flags(shape)
+    om = [1.8, 1.2, 1.4]
+    sim = Sim("D3Q27", "cumulant", storage, pattern, shape, periodic=(False, False, True), omega=om,
+              u_wall=(0.05, 0.0, 0.0), flags=fl)
+    P = inputs.random_pdfs(lat.w, shape[::-1], seed=23)
+    sim.set_state(P.reshape(lat.q, -1))
+    sim.step(4)
+    ref = olbm.Sim(oco.Method(lat, "cumulant", om), shape, periodic=(False, False, True), flags=fl,
+                   u_wall=(0.05, 0.0, 0.0))
+    ref.P = P.copy()
+    ref.step(4)
+    fluid = fl.reshape(-1) == 0
+    fg = sim.populations().cpu().numpy()[:, fluid]
+    fr = ref.populations().reshape(lat.q, -1)[:, fluid]
+    err = np.linalg.norm(fg - fr) / np.linalg.norm(fr - lat.w[:, None])
+    assert err < TOL[storage], err

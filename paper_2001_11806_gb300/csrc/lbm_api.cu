@@ -374,6 +374,11 @@ void fill_collide_params(lbm_ctx* c) {
   cp.smag_lambda = p.magic;
   c->kernel_op = p.collision == LBM_KBC ? OP_KBC : p.collision;
   if (cp.smag) c->kernel_op = p.collision == LBM_SRT ? OP_SRT_LES : OP_TRT_LES;
+  // MRT whose orders >= 3 share one rate: projector form (collide_mrt3);
+  // orders 5 and 6 exist for D3Q27 only
+  if (p.collision == LBM_MRT && om[2] == om[3] &&
+      (p.stencil != LBM_D3Q27 || (om[4] == om[2] && om[5] == om[2])))
+    c->kernel_op = OP_MRT3;
 }
 
 }  // namespace

@@ -22,8 +22,11 @@
 namespace lbm {
 
 // OP_SRT_LES / OP_TRT_LES: SRT / TRT with the Smagorinsky model compiled in;
-// OP_KBC: the entropic KBC operator
-enum Op : int { OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3, OP_SRT_LES = 4, OP_TRT_LES = 5, OP_KBC = 6 };
+// OP_KBC: the entropic KBC operator; OP_MRT3: MRT whose moments of order
+// >= 3 share one rate (see collide_mrt3)
+enum Op : int {
+  OP_SRT = 0, OP_TRT = 1, OP_MRT = 2, OP_CUM = 3, OP_SRT_LES = 4, OP_TRT_LES = 5, OP_KBC = 6, OP_MRT3 = 7
+};
 
 // Runtime parameters of a sweep, passed by value to the kernel.
 struct CollideParams {
@@ -352,6 +355,103 @@ __device__ __forceinline__ void collide_kbc(T (&v)[L::Q], const CollideParams& p
     const int q = 2 * k + 1;
     v[q] = fma(mh, e[k], v[q]);
     v[q + 1] = fma(mh, o[k], v[q + 1]);
+  }
+}
+
+// -------------------------------------------- MRT with one higher-order rate
+// MRT (Eq. mrt) with the w-orthogonal basis when every moment of order >= 3
+// relaxes with one rate omega_h: then M^-1 S M = omega_s P_s + omega_b P_b +
+// omega_h P_h with w-orthogonal projectors onto the shear moments, the bulk
+// moment and everything of order >= 3.  With y = h - h^eq + G/2 (mass and
+// momentum of y vanish: h^eq carries j + F/2, G carries F) the Guo-forced
+// update  h* = h - M^-1 S M y + G  becomes
+//   h* = h + G - omega_h y - (omega_s - omega_h) Ys - (omega_b - omega_h) Yb,
+// Ys_q = 4.5 w_q c_q.dev(Pi_y).c_q, Yb_q = (4.5 / D) w_q (|c_q|^2 - D/3) tr Pi_y,
+// Pi_y = sum c c y (the closed forms of the KBC operator above).  The result
+// equals the general pair-form MRT up to rounding, at about the cost of TRT.
+template <class L, class T>
+__device__ __forceinline__ void collide_mrt3(T (&h)[L::Q], const CollideParams& p) {
+  constexpr int NP = (L::Q - 1) / 2;
+  constexpr int D = L::D;
+  T s[NP], dd[NP];
+  T drho = h[0], jx = T(0), jy = T(0), jz = T(0);
+  bool ix = false, iy = false, iz = false;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    s[k] = h[q] + h[q + 1];
+    dd[k] = h[q] - h[q + 1];
+    drho += s[k];
+    acc_signed(jx, ix, L::cx(q), dd[k]);
+    acc_signed(jy, iy, L::cy(q), dd[k]);
+    acc_signed(jz, iz, L::cz(q), dd[k]);
+  }
+  T F[3] = {T(0), T(0), T(0)};
+  const bool force = p.has_force != 0;
+  if (force) {
+    F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
+    jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
+  }
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, D == 3 ? jz * inv : T(0)};
+  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T base = drho - T(1.5) * rho0 * usq;
+  const T k45 = T(4.5) * rho0, k3 = T(3) * rho0;
+  const T uF3 = T(3) * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
+  const T oh = rate<T>(p, 2);
+  const T cs = rate<T>(p, 0) - oh, cb = rate<T>(p, 1) - oh;
+  // pair sums of y (ys, kept in s) and Pi_y; odd parts need no projection
+  T pn[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    T Gs = T(0);
+    if (force) Gs = w * (T(9) * cu * cdot<L, T>(q, F) - uF3);
+    const T ys = s[k] - T(2) * w * fma(k45, cu * cu, base) + Gs;
+    const int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
+    if (cx) pn[0] += ys;
+    if (cy) pn[1] += ys;
+    if (cz) pn[2] += ys;
+    if (cx && cy) pn[3] += cx * cy > 0 ? ys : -ys;
+    if (cx && cz) pn[4] += cx * cz > 0 ? ys : -ys;
+    if (cy && cz) pn[5] += cy * cz > 0 ? ys : -ys;
+    s[k] = ys;
+  }
+  const T tr = pn[0] + pn[1] + pn[2];
+  const T mean = tr * T(1.0 / D);
+  pn[0] -= mean; pn[1] -= mean; pn[2] -= mean;
+  if (D == 2) pn[2] = T(0);
+  const T kb = T(4.5 / D) * tr;
+  {
+    const T w0 = T(L::w(0));
+    const T G0 = force ? -w0 * uF3 : T(0);
+    const T y0 = h[0] - w0 * base + T(0.5) * G0;
+    h[0] = h[0] + G0 - oh * y0 + cb * (T(1.5) * w0 * tr);
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = 2 * k + 1;
+    const T w = T(L::w(q));
+    const T cu = cdot<L, T>(q, u);
+    T Gs = T(0), Gd = T(0);
+    if (force) {
+      const T cF = cdot<L, T>(q, F);
+      Gs = w * (T(9) * cu * cF - uF3);
+      Gd = w * T(3) * cF;
+    }
+    const int c2 = L::cx(q) * L::cx(q) + L::cy(q) * L::cy(q) + L::cz(q) * L::cz(q);
+    const T proj = cs * (T(4.5) * w * kbc_quad<L, T>(q, pn)) + cb * (w * kb * T(c2 - D / 3.0));
+    // even part: s/2 + G+ - omega_h ys/2 - projections; odd part: d/2 + G- - omega_h yd/2
+    const T hs = T(0.5) * (h[q] + h[q + 1]);
+    const T hd = T(0.5) * (h[q] - h[q + 1]);
+    const T yd = dd[k] - T(2) * w * k3 * cu + Gd;
+    const T A = hs + Gs - T(0.5) * oh * s[k] - proj;
+    const T B = hd + Gd - T(0.5) * oh * yd;
+    h[q] = A + B;
+    h[q + 1] = A - B;
   }
 }
 

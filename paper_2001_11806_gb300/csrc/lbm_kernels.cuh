@@ -260,6 +260,11 @@ __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, st
   collide_mrt<L, T>(v, p);
 }
 template <class L, class T, bool DH>
+__device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_MRT3>) {
+  static_assert(DH, "MRT works on shifted populations");
+  collide_mrt3<L, T>(v, p);
+}
+template <class L, class T, bool DH>
 __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, std::integral_constant<int, OP_KBC>) {
   static_assert(DH, "KBC works on shifted populations");
   collide_kbc<L, T>(v, p);

@@ -18,6 +18,7 @@ struct Ops {
       case OP_SRT_LES: return launch_sweep_op<L, ST, OP_SRT_LES>(kind, bnd, a, s);
       case OP_TRT_LES: return launch_sweep_op<L, ST, OP_TRT_LES>(kind, bnd, a, s);
       case OP_KBC: return launch_sweep_op<L, ST, OP_KBC>(kind, bnd, a, s);
+      case OP_MRT3: return launch_sweep_op<L, ST, OP_MRT3>(kind, bnd, a, s);
       case OP_CUM:
         if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s);
         return cudaErrorInvalidValue;

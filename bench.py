@@ -255,6 +255,10 @@ def run_variants(device, peak):
                                                                   periodic=(False, False, False),
                                                                   u_wall=(0.05, 0, 0)),
          "channel", 300),
+        ("D3Q19 MRT FP32 channel 512x128x128 two-grid pull, separate boundary kernel",
+         dict(stencil="D3Q19", collision="mrt", storage="f32", pattern="pull", shape=(512, 128, 128),
+              omega=[1.7, 1.0, 1.0, 1.0], periodic=(False, False, False), u_wall=(0.05, 0, 0),
+              boundary="separate"), "channel", 300),
         ("D3Q19 MRT FP16-shifted channel 512x128x128 AA", dict(stencil="D3Q19", collision="mrt", storage="f16s",
                                                                  pattern="aa", shape=(512, 128, 128),
                                                                  omega=[1.7, 1.0, 1.0, 1.0],

@@ -94,6 +94,7 @@ enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F32S = 3 };
  *     axis the last layer (index n - 1) must be non-fluid (a wall, inlet or
  *     outlet layer); lbm_create returns LBM_E_UNSUPPORTED otherwise. */
 enum { LBM_PULL = 0, LBM_AA = 1, LBM_ESOTWIST = 2 };
+enum { LBM_BOUNDARY_IN_SWEEP = 0, LBM_BOUNDARY_SEPARATE = 1 };
 /* uint8 flag per cell; 0 = fluid.  A boundary link (x, q) takes its type from
  * the flag of its source cell x - c_q with precedence NOSLIP > INLET > OUTLET
  * (a non-zero flag with none of these bits counts as NOSLIP).  Sources outside
@@ -131,6 +132,16 @@ typedef struct lbm_params {
    * rate becomes a per-cell omega from the non-equilibrium stress (Sec. III-C,
    * turbulence models); with trt_magic the odd rate follows through Lambda. */
   double smagorinsky_cs;
+  /* LBM_BOUNDARY_IN_SWEEP (default): boundary links are resolved inside the
+   * sweep through the link mask.  LBM_BOUNDARY_SEPARATE (two-grid pull
+   * only): before every sweep a boundary kernel writes B_q(P(x)) into the
+   * slot of the link's non-fluid source cell, and the sweep streams every
+   * link as if it were fluid (Sec. IV-B "Boundary Conditions", the variant
+   * with separate boundary kernels).  Every boundary-link source must then
+   * lie inside the box: along a non-periodic axis the first and the last
+   * layer must be non-fluid (LBM_E_UNSUPPORTED otherwise, or for AA and the
+   * esoteric twist). */
+  int32_t boundary_mode;
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -214,7 +225,8 @@ lbm_status lbm_set_force(lbm_ctx* ctx, const double F[3]);
 
 /* One time step of the pull pattern from the population array src into dst
  * (both pdf_bytes, distinct; the context's own arrays are not touched).
- * LBM_E_STATE for an AA context.  Used to recompute checkpoint segments. */
+ * LBM_E_STATE for an AA context, LBM_E_UNSUPPORTED with separate boundary
+ * kernels.  Used to recompute checkpoint segments. */
 lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
 
 /* Discrete adjoint of one pull time step (the paper has no adjoint; this is
@@ -226,8 +238,8 @@ lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
  * when storage is LBM_F64, else FP32 (distinct).  P_prev: device population
  * array in the storage type.  Requires the pull pattern (LBM_E_STATE), SRT,
  * TRT or MRT without the Smagorinsky model (LBM_E_UNSUPPORTED for cumulant,
- * KBC and Smagorinsky) and no OUTLET links (LBM_E_UNSUPPORTED).  Non-fluid
- * cells receive zero. */
+ * KBC and Smagorinsky), boundary links resolved in the sweep and no OUTLET
+ * links (LBM_E_UNSUPPORTED).  Non-fluid cells receive zero. */
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* P_prev, const void* lam_in, void* lam_out,
                             double* dLdF);
 

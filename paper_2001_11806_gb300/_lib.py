@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
                 ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("periodic", c_int32 * 3),
                 ("omega", c_double * 6), ("trt_magic", c_int32), ("incompressible", c_int32),
                 ("magic", c_double), ("u_wall", c_double * 3), ("rho_outlet", c_double),
-                ("force", c_double * 3), ("smagorinsky_cs", c_double)]
+                ("force", c_double * 3), ("smagorinsky_cs", c_double), ("boundary_mode", c_int32)]
 
 
 _LIB = None

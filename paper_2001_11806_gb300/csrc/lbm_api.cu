@@ -194,6 +194,14 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
     *msg = "smagorinsky_cs must be >= 0";
     return LBM_E_INVAL;
   }
+  if (p->boundary_mode != LBM_BOUNDARY_IN_SWEEP && p->boundary_mode != LBM_BOUNDARY_SEPARATE) {
+    *msg = "unknown boundary_mode";
+    return LBM_E_INVAL;
+  }
+  if (p->boundary_mode == LBM_BOUNDARY_SEPARATE && p->pattern != LBM_PULL) {
+    *msg = "separate boundary kernels are built for the two-grid pull pattern";
+    return LBM_E_UNSUPPORTED;
+  }
   if (p->smagorinsky_cs > 0.0 && p->collision != LBM_SRT && p->collision != LBM_TRT) {
     *msg = "the Smagorinsky model is built for SRT and TRT";
     return LBM_E_UNSUPPORTED;
@@ -257,6 +265,7 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
   a.list = c->list;
   a.n_main = c->n_main;
   a.n_wrap = c->n_wrap;
+  a.boundary_mode = c->p.boundary_mode;
   for (int q = 0; q < 27; ++q) {
     const size_t off = q < c->q ? size_t(q) * size_t(c->N) * c->elem : 0;
     a.srcq[q] = src ? static_cast<const char*>(src) + off : nullptr;
@@ -303,6 +312,10 @@ cudaError_t sweep_once(lbm_ctx* c, cudaStream_t s, int64_t t, int cur) {
   if (c->p.pattern == LBM_PULL) {
     SweepArgs a = make_args(c, c->buf[cur], c->buf[1 - cur]);
     set_interior(a, c, K_PULL);
+    if (c->has_mask && c->p.boundary_mode == LBM_BOUNDARY_SEPARATE) {
+      const cudaError_t e = c->ops.boundary_pull(a, c->buf[cur], s);
+      if (e != cudaSuccess) return e;
+    }
     return c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, s);
   }
   SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
@@ -477,6 +490,11 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
       delete c;
       return LBM_E_UNSUPPORTED;
     }
+    if (p->boundary_mode == LBM_BOUNDARY_SEPARATE &&
+        (c->link_types & (TYPES_FLUID_FIRST_LAYER | TYPES_FLUID_LAST_LAYER))) {
+      delete c;
+      return LBM_E_UNSUPPORTED;
+    }
     c->list = reinterpret_cast<int*>(static_cast<char*>(aux) + lay.list_off);
     const lbm_status ls = build_list(c, a, lay);
     if (ls != LBM_OK) {
@@ -619,6 +637,7 @@ lbm_status lbm_set_force(lbm_ctx* c, const double F[3]) {
 lbm_status lbm_step_pull(lbm_ctx* c, const void* src, void* dst) {
   if (!c || !src || !dst || src == dst) return LBM_E_INVAL;
   if (c->p.pattern != LBM_PULL) return LBM_E_STATE;
+  if (c->p.boundary_mode == LBM_BOUNDARY_SEPARATE) return LBM_E_UNSUPPORTED;
   SweepArgs a = make_args(c, src, dst);
   set_interior(a, c, K_PULL);
   cudaError_t e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
@@ -641,6 +660,10 @@ lbm_status adjoint_ok(lbm_ctx* c) {
   }
   if (c->cp.smag) {
     c->err = "the Smagorinsky model is not differentiated";
+    return LBM_E_UNSUPPORTED;
+  }
+  if (c->p.boundary_mode == LBM_BOUNDARY_SEPARATE) {
+    c->err = "the adjoint works with boundary links resolved in the sweep";
     return LBM_E_UNSUPPORTED;
   }
   return LBM_OK;

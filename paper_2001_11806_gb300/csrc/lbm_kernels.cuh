@@ -47,6 +47,9 @@ __host__ __device__ constexpr int eso_rd(int c) { return c < 0 ? 1 : 0; }
 // layer non-fluid: its wrapped locations are shared with the first layer,
 // whose boundary links would then race with the fluid cells there.
 constexpr unsigned TYPES_FLUID_LAST_LAYER = 1u << 8;
+// ... and when a fluid cell lies in the first layer of a non-periodic axis
+// (a boundary link whose source is outside the box)
+constexpr unsigned TYPES_FLUID_FIRST_LAYER = 1u << 9;
 __host__ __device__ constexpr int eso_wr(int c) { return c > 0 ? 1 : 0; }
 
 struct Geom {
@@ -79,6 +82,7 @@ struct SweepArgs {
   // neighbour accesses followed by n_wrap with
   const int* list;
   int n_main, n_wrap;
+  int boundary_mode;  // LBM_BOUNDARY_SEPARATE: the sweep streams every link as fluid
 };
 
 constexpr int kBlockX = 128;
@@ -392,11 +396,12 @@ __device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& 
 
 // 0: not fluid; 1: plain (no wrapped neighbour access, no inlet or outlet
 // link); 2: on a face of a periodic axis or with an inlet or outlet link
+// (the latter only for sweeps that resolve boundary links themselves)
 template <class L>
 __device__ __forceinline__ int list_category(const SweepArgs& a, long long cell) {
   const uint32_t m = a.mask[cell];
   if (m & MASK_SOLID) return 0;
-  if (m & MASK_SPECIAL) return 2;
+  if ((m & MASK_SPECIAL) && !a.boundary_mode) return 2;
   int x, y, z;
   cell_coords(a.g, cell, x, y, z);
   bool wrap = (a.g.per[0] && (x == 0 || x == a.g.nx - 1)) || (a.g.per[1] && (y == 0 || y == a.g.ny - 1));
@@ -483,7 +488,8 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (WRAP ? a.n_wrap : a.n_main)) return;
   const int cell = a.list[WRAP ? a.n_main + i : i];
-  const uint32_t mask = a.mask[cell];
+  // with a separate boundary kernel every link streams as a fluid link
+  const uint32_t mask = a.boundary_mode ? 0u : a.mask[cell];
   T v[L::Q];
   if constexpr (WRAP) {
     int x, y, z;
@@ -604,7 +610,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
     int tx;
     asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
     const int cs = a.list[blockIdx.x * blockDim.x + tx];
-    const uint32_t ms = a.mask[cs];
+    const uint32_t ms = a.boundary_mode ? 0u : a.mask[cs];
     const unsigned N = unsigned(a.g.N);
     const int nx = a.g.nx, nxy = a.g.nx * a.g.ny;
 #pragma unroll
@@ -626,6 +632,52 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
       }
       reinterpret_cast<S*>(a.dstq[lo])[idx] = D::store(v[q], L::w(q));
     }
+  }
+}
+
+// Separate boundary kernel of the two-grid pull (LBM_BOUNDARY_SEPARATE):
+// for every boundary link (x, q) of a fluid cell it writes B_q(P(x)) into
+// slot q of the link's source cell x - c_q (inside the box, non-fluid), so
+// that the following sweep can stream the link like a fluid one.  Each such
+// slot belongs to one link; fluid cells' slots are only read.
+template <class L, class ST>
+__global__ void __launch_bounds__(kBlockX) k_boundary_pull(const SweepArgs a, typename ST::S* __restrict__ P) {
+  using T = typename ST::T;
+  using S = typename ST::S;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_main + a.n_wrap) return;
+  const int cell = a.list[i];
+  const uint32_t mask = a.mask[cell];
+  if ((mask & ((1u << L::Q) - 2u)) == 0) return;
+  int x, y, z;
+  cell_coords(a.g, cell, x, y, z);
+  constexpr bool DH = ST::shifted;  // the storage's own value domain
+  using D = Dom<ST, DH>;
+  const long long N = a.g.N;
+  if (!(mask & MASK_SPECIAL)) {
+    // no inlet or outlet link: every boundary link is a no-slip copy
+    const Nbr nb = make_nbr(a.g, x, y, z);
+#pragma unroll
+    for (int q = 1; q < L::Q; ++q)
+      if ((mask >> q) & 1u) P[q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q))] = P[opp(q) * N + cell];
+    return;
+  }
+  T up[3] = {T(0), T(0), T(0)};
+  {
+    T v[L::Q];
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) v[k] = D::load(P[k * N + cell], L::w(k));
+    post_velocity<L, T, DH>(v, outlet_params(a.cp), up);
+  }
+  const Nbr nb = make_nbr(a.g, x, y, z);
+#pragma unroll
+  for (int q = 1; q < L::Q; ++q) {
+    if (!((mask >> q) & 1u)) continue;
+    const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+    S* slot = P + q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+    if (t == L_OUTLET) *slot = D::store(outlet_value<L, T, DH>(q, up, outlet_params(a.cp)), L::w(q));
+    else if (t == L_INLET) *slot = D::store(D::load(P[opp(q) * N + cell], L::w(q)) + ubb_term<L, T>(q, a.cp), L::w(q));
+    else *slot = P[opp(q) * N + cell];  // no-slip: the stored value itself
   }
 }
 
@@ -1023,6 +1075,8 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsi
     if (types != nullptr && ((!a.g.per[0] && x == a.g.nx - 1) || (!a.g.per[1] && y == a.g.ny - 1) ||
                              (!a.g.per[2] && z == a.g.nz - 1)))
       atomicOr(types, TYPES_FLUID_LAST_LAYER);
+    if (types != nullptr && ((!a.g.per[0] && x == 0) || (!a.g.per[1] && y == 0) || (!a.g.per[2] && z == 0)))
+      atomicOr(types, TYPES_FLUID_FIRST_LAYER);
     uint32_t m = 0;
     for (int q = 1; q < L::Q; ++q) {
       int sx = x - L::cx(q), sy = y - L::cy(q), sz = z - L::cz(q);

@@ -89,6 +89,14 @@ cudaError_t launch_link_mask(const SweepArgs& a, uint32_t* mask, unsigned* types
   return cudaGetLastError();
 }
 
+template <class L, class ST>
+cudaError_t launch_boundary_pull(const SweepArgs& a, void* P, cudaStream_t s) {
+  const int n = a.n_main + a.n_wrap;
+  if (n > 0)
+    k_boundary_pull<L, ST><<<(n + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(a, static_cast<typename ST::S*>(P));
+  return cudaGetLastError();
+}
+
 template <class L>
 cudaError_t launch_list_count(const SweepArgs& a, int nblk, int* counts, cudaStream_t s) {
   k_list_count<L><<<nblk, kListThreads, 0, s>>>(a, nblk, counts);
@@ -115,6 +123,7 @@ struct OpsTable {
   cudaError_t (*eq_vjp)(const SweepArgs&, const double*, const double*, const void*, double*, cudaStream_t);
   cudaError_t (*list_count)(const SweepArgs&, int, int*, cudaStream_t);
   cudaError_t (*list_scatter)(const SweepArgs&, int, const int*, int*, cudaStream_t);
+  cudaError_t (*boundary_pull)(const SweepArgs&, void*, cudaStream_t);
 };
 
 template <class L, class ST>
@@ -122,7 +131,7 @@ OpsTable make_table() {
   return OpsTable{&Ops<L, ST>::sweep,          &Ops<L, ST>::populations, &Ops<L, ST>::macroscopic,
                   &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>,
                   &Ops<L, ST>::adjoint,        &Ops<L, ST>::ke_seed,     &Ops<L, ST>::eq_vjp,
-                  &launch_list_count<L>,       &launch_list_scatter<L>};
+                  &launch_list_count<L>,       &launch_list_scatter<L>,  &launch_boundary_pull<L, ST>};
 }
 
 #define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();

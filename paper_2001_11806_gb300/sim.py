@@ -25,7 +25,7 @@ class Sim:
     def __init__(self, stencil="D3Q19", collision="trt", storage="f32", pattern="pull", shape=(1, 1, 1),
                  periodic=(True, True, True), omega=(1.0,), trt_magic=None, incompressible=False,
                  u_wall=(0.0, 0.0, 0.0), rho_outlet=1.0, force=(0.0, 0.0, 0.0), flags=None,
-                 device="cuda:0", stream=None, smagorinsky_cs=0.0):
+                 device="cuda:0", stream=None, smagorinsky_cs=0.0, boundary="in_sweep"):
         L = lib()
         self.device = torch.device(device)
         p = Params()
@@ -49,6 +49,7 @@ class Sim:
             p.force[i] = float(force[i])
         p.rho_outlet = float(rho_outlet)
         p.smagorinsky_cs = float(smagorinsky_cs)
+        p.boundary_mode = {"in_sweep": 0, "separate": 1}[boundary]
         self.params = p
         self.stencil, self.collision, self.storage, self.pattern = stencil, collision, storage, pattern
         self.shape = tuple(int(v) for v in shape)

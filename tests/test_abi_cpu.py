@@ -75,7 +75,8 @@ def test_query_sizes(L):
     (dict(rho_outlet=-1.0), 1), (dict(collision=1, trt_magic=1, magic=-1.0), 1),
     (dict(collision=4, omega=[1.9, 0.0]), 1), (dict(collision=4, omega=[1.9, 1.0], force=(1e-4, 0.0, 0.0)), 2),
     (dict(collision=4, omega=[1.9, 1.0], smagorinsky_cs=0.1), 2), (dict(collision=2, smagorinsky_cs=0.1), 2),
-    (dict(collision=5), 1),
+    (dict(collision=5), 1), (dict(boundary_mode=2), 1), (dict(boundary_mode=1, pattern=1), 2),
+    (dict(boundary_mode=1, pattern=2), 2),
 ])
 def test_invalid_parameters(L, kw, status):
     s, _, _ = _query(_params(**kw))

@@ -16,8 +16,9 @@
  *   - two-array stream-pull-collide and single-array AA and esoteric-twist
  *     update patterns
  *     (Sec. IV-B "Streaming and Collision");
- *   - per-link boundaries compiled into the sweep through a flag field
- *     (Sec. IV-B "Boundary Conditions"): halfway bounce-back, velocity
+ *   - per-link boundaries through a flag field (Sec. IV-B "Boundary
+ *     Conditions"), compiled into the sweep or, for the two-array pattern,
+ *     in a separate boundary kernel: halfway bounce-back, velocity
  *     bounce-back (UBB listing of Sec. III-C) and an equilibrium outlet;
  *   - Guo body forcing (forcing schemes cited in Sec. I);
  *   - a discrete adjoint of the time step (not in the paper).
@@ -117,6 +118,8 @@ typedef struct lbm_params {
    *   TRT: omega[0] = omega_e (even moments), omega[1] = omega_o (odd).
    *   MRT: shear, bulk, 3rd-order, 4th-order, 5th-order, 6th-order rates
    *        (orders 5 and 6 exist for D3Q27 only); conserved moments use 0.
+   *        When all orders >= 3 share one rate the sweep uses an equivalent
+   *        projector form of the operator (same result up to rounding).
    *   CUMULANT: shear, bulk, higher-order (orders >= 3).
    *   KBC: omega[0] = shear rate omega_s, omega[1] = bulk rate (equal to
    *        omega[0] gives the paper's two-rate form); the rate of orders >= 3

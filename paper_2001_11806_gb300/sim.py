@@ -6,6 +6,12 @@ does all the work.
     sim.init_equilibrium(rho, u)        # torch/numpy FP64, [N] and [d][N]
     sim.step(1000)
     rho, u = sim.macroscopic()
+
+stencil "D2Q9" | "D3Q19" | "D3Q27"; collision "srt" | "trt" | "mrt" |
+"cumulant" | "kbc"; storage "f64" | "f32" | "f32s" | "f16s" (s = shifted,
+h = f - w); pattern "pull" | "aa" | "eso" (esoteric twist); boundary
+"in_sweep" | "separate" (separate boundary kernel, pull only); omega as in
+lbm_params.omega of include/lbm.h.
 """
 import ctypes
 

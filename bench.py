@@ -221,10 +221,12 @@ def _time_steps(sim, steps, torch):
     return e0.elapsed_time(e1) / steps
 
 
-def run_variants(device, peak):
+def run_variants(device, peak, only=None, steps_override=None, warmup=10):
     """The other workloads of the metric, one line each: MLUPS over all cells,
     algorithmic GB/s (2 q sizeof per fluid cell, plus the 4 B link mask per
-    cell when boundaries are present) and its fraction of the measured peak."""
+    cell when boundaries are present) and its fraction of the measured peak.
+    only: run just the workloads whose name contains this string (and not the
+    adjoint line), with steps_override timed steps after `warmup` steps."""
     import torch
 
     from paper_2001_11806_gb300 import inputs
@@ -272,8 +274,14 @@ def run_variants(device, peak):
         ("D2Q9 SRT FP64 64^2 pull", dict(stencil="D2Q9", collision="srt", storage="f64", pattern="pull",
                                          shape=(64, 64, 1), omega=[1.6]), "tgv2d", 2000),
     ]
+    if only is not None:
+        specs = [sp for sp in specs if only in sp[0]]
+        if not specs:
+            raise SystemExit(f"no variant matches {only!r}")
     flags_channel = None
     for name, kw, init, steps in specs:
+        if steps_override is not None:
+            steps = steps_override
         flags = None
         if init == "channel":
             if flags_channel is None:
@@ -288,7 +296,7 @@ def run_variants(device, peak):
         else:
             rho, u = np.ones(N), np.zeros((3, N))
         sim.init_equilibrium(rho.reshape(-1), u.reshape(sim.d, -1))
-        sim.step(10)
+        sim.step(warmup)
         ms = _time_steps(sim, steps, torch)
         fluid = N if flags is None else int((flags == 0).sum())
         nbytes = 2 * q * elem[kw["storage"]] * fluid + (4 * N if flags is not None else 0)
@@ -299,6 +307,8 @@ def run_variants(device, peak):
         sim.close()
         del sim
         torch.cuda.empty_cache()
+    if only is not None:
+        return out
     # adjoint step cost against the forward step (D3Q19 TRT FP32 128^3)
     from paper_2001_11806_gb300 import _lib
     sim = Sim("D3Q19", "trt", "f32", "pull", (128,) * 3, omega=[OMEGA_E], trt_magic=MAGIC, force=[1e-6, 0, 0],
@@ -531,9 +541,19 @@ def main():
     ap.add_argument("--size", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    # run one variant workload alone (name substring), e.g. to profile it
+    ap.add_argument("--variant", default=None)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.variant is not None:
+        import torch
+        torch.cuda.set_device(0)
+        peak = measured_peak()[0]
+        for v in run_variants(torch.device("cuda:0"), peak, only=args.variant, steps_override=args.steps,
+                              warmup=args.warmup):
+            print(json.dumps(v))
+        return 0
     world, rank, local = dist_setup()
     if args.impl == "reference":
         rc = run_reference(args, world, rank)

@@ -272,6 +272,7 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
     a.dstq[q] = dst ? static_cast<char*>(dst) + off : nullptr;
     a.srci[q] = nullptr;
     a.dsti[q] = nullptr;
+    a.lf[q] = a.lb[q] = a.sf[q] = a.sb[q] = 0u;
   }
   return a;
 }
@@ -290,6 +291,29 @@ void set_interior(SweepArgs& a, const lbm_ctx* c, int kind) {
   auto shift = [](const void* p, long long bytes) {
     return reinterpret_cast<char*>(reinterpret_cast<uintptr_t>(p) + bytes);
   };
+  // element offsets of the masked sweeps (SweepArgs::lf, lb, sf, sb)
+  const unsigned uN = unsigned(c->N);
+  for (int q = 0; q < c->q; ++q) {
+    const int cx = cv[3 * q], cy = cv[3 * q + 1], cz = cv[3 * q + 2];
+    const int qb = q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1);
+    const int lo = q < qb ? q : qb;
+    const unsigned e = unsigned(cx + nx * cy + nxy * cz);
+    const unsigned w = unsigned(eso_wr(cx) + nx * eso_wr(cy) + nxy * eso_wr(cz));
+    auto up = [&](int slot) { return slot != lo ? uN : 0u; };
+    if (kind == K_PULL) {
+      a.lf[q] = up(q) - e;
+      a.lb[q] = up(qb);
+    } else if (kind == K_AA_ODD) {
+      a.lf[q] = up(qb) - e;
+      a.lb[q] = up(q);
+      a.sf[q] = up(q) + e;
+      a.sb[q] = up(qb);
+    } else if (kind == K_ESO_EVEN || kind == K_ESO_ODD) {
+      const int sn = kind == K_ESO_EVEN ? qb : q, so = kind == K_ESO_EVEN ? q : qb;
+      a.sf[q] = up(sn) + w;
+      a.sb[q] = up(so) + w;
+    }
+  }
   for (int q = 0; q < c->q; ++q) {
     const int cx = cv[3 * q], cy = cv[3 * q + 1], cz = cv[3 * q + 2];
     const long long off = (cx + nx * cy + nxy * cz) * el;

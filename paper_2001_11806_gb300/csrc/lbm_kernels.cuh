@@ -83,6 +83,11 @@ struct SweepArgs {
   const int* list;
   int n_main, n_wrap;
   int boundary_mode;  // LBM_BOUNDARY_SEPARATE: the sweep streams every link as fluid
+  // masked sweeps: element offsets, relative to the cell and to the stream of
+  // the lower slot of the pair (q, qbar), of the population direction q
+  // reads (lf: fluid link, lb: boundary link) and writes (sf, sb: fluid or
+  // boundary link (x, qbar)); unsigned, added modulo 2^32
+  unsigned lf[27], lb[27], sf[27], sb[27];
 };
 
 constexpr int kBlockX = 128;
@@ -516,11 +521,9 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
     }
   } else {
     // The two slots a direction can touch, q and qbar, are adjacent streams:
-    // one base (the lower slot) and an unsigned 32-bit element offset that
-    // adds N for the upper one (cell +- c_q stays inside the box here, and
-    // 2 N - 1 < 2^32).
-    const unsigned N = unsigned(a.g.N);
-    const int nx = a.g.nx, nxy = a.g.nx * a.g.ny;
+    // one base (the lower slot) plus a per-direction offset from the kernel
+    // arguments, selected by the boundary bit (the element index stays below
+    // 2 N - 1 < 2^32)
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) {
       const bool b = (mask >> q) & 1u;
@@ -532,9 +535,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
         // pull: fluid src[q][x - c_q], boundary src[qbar][x];
         // AA odd: fluid A[qbar][x - c_q], boundary A[q][x]
         const int lo = q < opp(q) ? q : opp(q);
-        const int sf = KIND == K_PULL ? q : opp(q), sb = KIND == K_PULL ? opp(q) : q;
-        const int off = L::cx(q) + nx * L::cy(q) + nxy * L::cz(q);
-        const unsigned idx = unsigned(b ? cell : cell - off) + ((b ? sb : sf) != lo ? N : 0u);
+        const unsigned idx = unsigned(cell) + (b ? a.lb[q] : a.lf[q]);
         v[q] = D::load(reinterpret_cast<const S*>(a.srcq[lo])[idx], L::w(q));
       }
     }
@@ -611,25 +612,15 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
     asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
     const int cs = a.list[blockIdx.x * blockDim.x + tx];
     const uint32_t ms = a.boundary_mode ? 0u : a.mask[cs];
-    const unsigned N = unsigned(a.g.N);
-    const int nx = a.g.nx, nxy = a.g.nx * a.g.ny;
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) {
+      // AA odd: fluid A[q][x + c_q], boundary link (x, qbar) A[qbar][x];
+      // esoteric twist: slot qbar (even) or q (odd) at x + max(c_q, 0), a
+      // boundary link takes the other slot of the same location
       const int p = opp(q);
       const bool b = (ms >> p) & 1u;
       const int lo = q < p ? q : p;
-      unsigned idx;
-      if constexpr (ESO) {
-        // slot qbar (even) or q (odd) at x + max(c_q, 0); a boundary link
-        // takes the other slot of the same location
-        const int sn = KIND == K_ESO_EVEN ? p : q, sb = KIND == K_ESO_EVEN ? q : p;
-        const int wr = eso_wr(L::cx(q)) + nx * eso_wr(L::cy(q)) + nxy * eso_wr(L::cz(q));
-        idx = unsigned(cs + wr) + ((b ? sb : sn) != lo ? N : 0u);
-      } else {
-        // AA odd: fluid A[q][x + c_q], boundary A[qbar][x]
-        const int off = L::cx(q) + nx * L::cy(q) + nxy * L::cz(q);
-        idx = unsigned(b ? cs : cs + off) + ((b ? p : q) != lo ? N : 0u);
-      }
+      const unsigned idx = unsigned(cs) + (b ? a.sb[q] : a.sf[q]);
       reinterpret_cast<S*>(a.dstq[lo])[idx] = D::store(v[q], L::w(q));
     }
   }

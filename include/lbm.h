@@ -70,7 +70,10 @@ typedef enum lbm_status {
   LBM_E_NOMEM = 4,       /* host allocation failed */
   LBM_E_BUFSIZE = 5,     /* a caller buffer is smaller than required */
   LBM_E_NONFINITE = 6,   /* a reduction found NaN or Inf */
-  LBM_E_BOUNDS = 7,      /* reserved: out-of-bounds index caught by a debug build */
+  LBM_E_BOUNDS = 7,      /* a kernel addressed memory outside the population arrays;
+                          * only a library built with LBM_DEBUG_BOUNDS checks this
+                          * (lbm_init_equilibrium, lbm_set_state, lbm_step and
+                          * lbm_step_pull then synchronise and report it) */
   LBM_E_STATE = 8        /* call not valid in the current state */
 } lbm_status;
 
@@ -291,6 +294,14 @@ lbm_status lbm_sync(lbm_ctx* ctx);
 const char* lbm_status_str(lbm_status s);
 /* Last error message of this context ("" if none); never NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Test hook for the failure paths (the paper has no counterpart): the next n
+ * host allocations made by the library fail, so that the calls making them
+ * return LBM_E_NOMEM (lbm_create allocates its context; a context with a
+ * flag field also allocates the offsets of its fluid-cell list).  n <= 0
+ * clears the request.  Process-wide, not thread-specific. */
+void lbm_debug_fail_host_allocs(int32_t n);
+
 void lbm_destroy(lbm_ctx* ctx);
 
 #ifdef __cplusplus

@@ -8,7 +8,9 @@ import ctypes
 import os
 from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_uint8, c_uint32, c_void_p
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbm.so")
+# LBM_DEBUG_BOUNDS=1 selects the bounds-checking build (build(debug_bounds=True))
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "liblbm_debug.so" if os.environ.get("LBM_DEBUG_BOUNDS") == "1" else "liblbm.so")
 
 STENCILS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
 COLLISIONS = {"srt": 0, "trt": 1, "mrt": 2, "cumulant": 3, "kbc": 4}
@@ -62,6 +64,7 @@ _SIGS = {
     "lbm_reduce_noalloc": (c_int32, [POINTER(Params), c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "lbm_sync": (c_int32, [c_void_p]),
     "lbm_status_str": (c_char_p, [c_int32]),
+    "lbm_debug_fail_host_allocs": (None, [c_int32]),
     "lbm_last_error": (c_char_p, [c_void_p]),
     "lbm_destroy": (None, [c_void_p]),
 }

@@ -17,6 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
+LIB_DEBUG = os.path.join(PKG, "liblbm_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-lineinfo",
          "-I", os.path.join(ROOT, "include")]
@@ -34,8 +35,8 @@ def _newest_header():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _newest_header()):
         return obj, ""
     cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
@@ -45,27 +46,35 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, ptxas_info=False, jobs=None):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, ptxas_info=False, jobs=None, debug_bounds=False):
+    """Build liblbm.so; debug_bounds=True builds liblbm_debug.so instead, whose
+    sweep kernels check every population access (LBM_DEBUG_BOUNDS, loaded by
+    the binding when the environment sets LBM_DEBUG_BOUNDS=1)."""
+    build_dir = BUILD + "_debug" if debug_bounds else BUILD
+    lib = LIB_DEBUG if debug_bounds else LIB
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug_bounds:
+        extra = extra + ["-DLBM_DEBUG_BOUNDS"]
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + ".tmp"
+    LIB_OUT = lib
+    if not os.path.exists(LIB_OUT) or os.path.getmtime(LIB_OUT) < max(os.path.getmtime(o) for o in objs):
+        tmp = LIB_OUT + ".tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, LIB_OUT)
+    return LIB_OUT
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, ptxas_info="--ptxas" in sys.argv))
+    print(build(verbose="-v" in sys.argv, ptxas_info="--ptxas" in sys.argv, debug_bounds="--debug-bounds" in sys.argv))

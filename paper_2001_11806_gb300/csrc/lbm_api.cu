@@ -2,12 +2,12 @@
 // bookkeeping and dispatch to the kernels instantiated per stencil/storage.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <string>
-#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_ops.cuh"
@@ -74,7 +74,7 @@ struct lbm_ctx {
   int kernel_op = 0;  // collision operator of the sweep kernels (LES variants included)
   CollideParams cp;
   OpsTable ops;
-  std::string err;
+  char err[256] = {0};  // last error text; fixed storage, so reporting never allocates
   // Small domains: lbm_step replays kGraphSteps sweeps as one CUDA graph
   // (recorded on a private stream; index = pull buffer holding P, 0 for the
   // single-array patterns, which start a graph at even parity).
@@ -135,7 +135,7 @@ Layout layout_for(const lbm_params& p, long long N) {
 bool rate_ok(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
 
 // Validate parameters; fills msg on failure.
-lbm_status validate(const lbm_params* p, std::string* msg) {
+lbm_status validate(const lbm_params* p, const char** msg) {
   if (!p) { *msg = "params is NULL"; return LBM_E_INVAL; }
   if (p->stencil < LBM_D2Q9 || p->stencil > LBM_D3Q27) { *msg = "unknown stencil"; return LBM_E_INVAL; }
   if (p->collision < LBM_SRT || p->collision > LBM_KBC) { *msg = "unknown collision"; return LBM_E_INVAL; }
@@ -209,17 +209,40 @@ lbm_status validate(const lbm_params* p, std::string* msg) {
   return LBM_OK;
 }
 
+// Last-error text, truncated to the fixed buffer.
+void set_err(lbm_ctx* c, const char* a, const char* b = "", const char* d = "") {
+  std::snprintf(c->err, sizeof(c->err), "%s%s%s", a, b, d);
+}
+
+// Host allocations that lbm_debug_fail_host_allocs asked to fail.
+std::atomic<int> g_fail_allocs{0};
+bool injected_alloc_failure() {
+  int n = g_fail_allocs.load();
+  while (n > 0)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+  return false;
+}
+
 // Fluid-cell list of a masked domain (see k_sweep_list): per-chunk counts on
 // the device, exclusive offsets on the host, ordered scatter on the device.
 lbm_status build_list(lbm_ctx* c, const SweepArgs& a, const Layout& lay) {
   int* counts = reinterpret_cast<int*>(static_cast<char*>(c->aux) + lay.count_off);
   const int nblk = lay.nblk;
+  const size_t nh = size_t(nblk) * 2;
+  int* h = injected_alloc_failure() ? nullptr : static_cast<int*>(std::malloc(nh * sizeof(int)));
+  if (!h) {
+    set_err(c, "host allocation of the list offsets failed");
+    return LBM_E_NOMEM;
+  }
+  struct Free {
+    int* p;
+    ~Free() { std::free(p); }
+  } guard{h};
   cudaError_t e = c->ops.list_count(a, nblk, counts, c->stream);
-  std::vector<int> h(size_t(nblk) * 2);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), counts, h.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts, nh * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
-    c->err = std::string("list count: ") + cudaGetErrorString(e);
+    set_err(c, "list count: ", cudaGetErrorString(e));
     return LBM_E_CUDA;
   }
   long long n_main = 0;
@@ -234,19 +257,44 @@ lbm_status build_list(lbm_ctx* c, const SweepArgs& a, const Layout& lay) {
   }
   c->n_main = int(n_main);
   c->n_wrap = int(run2 - n_main);
-  e = cudaMemcpyAsync(counts, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  e = cudaMemcpyAsync(counts, h, nh * sizeof(int), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = c->ops.list_scatter(a, nblk, counts, c->list, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
-    c->err = std::string("list scatter: ") + cudaGetErrorString(e);
+    set_err(c, "list scatter: ", cudaGetErrorString(e));
     return LBM_E_CUDA;
   }
   return LBM_OK;
 }
 
 lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
-  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  set_err(c, where, ": ", cudaGetErrorString(e));
   return LBM_E_CUDA;
+}
+
+// Device word of the bounds-checking build (in the aux result area).
+unsigned* bounds_word(const lbm_ctx* c) {
+  return c->result ? reinterpret_cast<unsigned*>(reinterpret_cast<char*>(c->result) + 72) : nullptr;
+}
+
+// Bounds-checking build: waits for the stream and turns a recorded
+// out-of-array access into LBM_E_BOUNDS (the word is cleared).  Otherwise a
+// no-op.
+lbm_status debug_check(lbm_ctx* c) {
+#ifdef LBM_DEBUG_BOUNDS
+  unsigned word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, bounds_word(c), sizeof(word), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return LBM_E_CUDA;
+  if (word) {
+    cudaMemsetAsync(bounds_word(c), 0, sizeof(unsigned), c->stream);
+    std::snprintf(c->err, sizeof(c->err), "a kernel accessed memory outside the population arrays");
+    return LBM_E_BOUNDS;
+  }
+#else
+  (void)c;
+#endif
+  return LBM_OK;
 }
 
 SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
@@ -266,6 +314,8 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
   a.n_main = c->n_main;
   a.n_wrap = c->n_wrap;
   a.boundary_mode = c->p.boundary_mode;
+  a.pdf_bytes = c->pdf_bytes;
+  a.bounds_flag = bounds_word(c);
   for (int q = 0; q < 27; ++q) {
     const size_t off = q < c->q ? size_t(q) * size_t(c->N) * c->elem : 0;
     a.srcq[q] = src ? static_cast<const char*>(src) + off : nullptr;
@@ -454,7 +504,7 @@ lbm_status lbm_stencil_info(int32_t stencil, int32_t* q, int32_t* d, int32_t* c,
 }
 
 lbm_status lbm_query_sizes(const lbm_params* p, size_t* pdf_bytes, size_t* aux_bytes) {
-  std::string msg;
+  const char* msg = "";
   const lbm_status s = validate(p, &msg);
   if (s != LBM_OK) return s;
   const long long N = (long long)p->nx * p->ny * p->nz;
@@ -467,7 +517,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
                       size_t pdf2_bytes, void* aux, size_t aux_bytes, const uint8_t* flags, void* stream) {
   if (!out) return LBM_E_INVAL;
   *out = nullptr;
-  std::string msg;
+  const char* msg = "";
   lbm_status s = validate(p, &msg);
   if (s != LBM_OK) return s;
   const long long N = (long long)p->nx * p->ny * p->nz;
@@ -478,7 +528,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
   if (p->pattern == LBM_PULL && !pdf2) return LBM_E_INVAL;
   if (pdf_bytes < need || (p->pattern == LBM_PULL && pdf2_bytes < need) || aux_bytes < lay.total)
     return LBM_E_BUFSIZE;
-  lbm_ctx* c = new (std::nothrow) lbm_ctx;
+  lbm_ctx* c = injected_alloc_failure() ? nullptr : new (std::nothrow) lbm_ctx;
   if (!c) return LBM_E_NOMEM;
   c->p = *p;
   c->q = stencil_q(p->stencil);
@@ -498,6 +548,12 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
   c->stream = static_cast<cudaStream_t>(stream);
   fill_collide_params(c);
   c->ops = get_table(p->stencil, p->storage);
+#ifdef LBM_DEBUG_BOUNDS
+  if (cudaMemsetAsync(bounds_word(c), 0, sizeof(unsigned), c->stream) != cudaSuccess) {
+    delete c;
+    return LBM_E_CUDA;
+  }
+#endif
   if (mask) {
     SweepArgs a = make_args(c, nullptr, nullptr);
     unsigned* types = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(c->result) + 64);
@@ -543,7 +599,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* u) 
   cudaError_t e = c->ops.set_state(c->p.pattern, 1, a, nullptr, rho, u, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init_equilibrium");
   c->t = 0;
-  return LBM_OK;
+  return debug_check(c);
 }
 
 lbm_status lbm_set_state(lbm_ctx* c, const double* P) {
@@ -553,7 +609,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* P) {
   cudaError_t e = c->ops.set_state(c->p.pattern, 0, a, P, nullptr, nullptr, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
   c->t = 0;
-  return LBM_OK;
+  return debug_check(c);
 }
 
 lbm_status lbm_step(lbm_ctx* c, int32_t n) {
@@ -568,6 +624,8 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
       if (e != cudaSuccess) return cuda_fail(c, e, "step graph");
       c->t += kGraphSteps;
       n -= kGraphSteps;
+      const lbm_status d = debug_check(c);
+      if (d != LBM_OK) return d;
       continue;
     }
     const cudaError_t e = sweep_once(c, c->stream, c->t, c->cur);
@@ -575,6 +633,8 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     if (c->p.pattern == LBM_PULL) c->cur = 1 - c->cur;
     ++c->t;
     --n;
+    const lbm_status d = debug_check(c);
+    if (d != LBM_OK) return d;
   }
   return LBM_OK;
 }
@@ -615,7 +675,7 @@ lbm_status lbm_reduce(lbm_ctx* c, double out[5]) {
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce sync");
   for (int i = 0; i < 5; ++i)
     if (!std::isfinite(out[i])) {
-      c->err = "reduction produced a non-finite value";
+      set_err(c, "reduction produced a non-finite value");
       return LBM_E_NONFINITE;
     }
   return LBM_OK;
@@ -665,29 +725,29 @@ lbm_status lbm_step_pull(lbm_ctx* c, const void* src, void* dst) {
   SweepArgs a = make_args(c, src, dst);
   set_interior(a, c, K_PULL);
   cudaError_t e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
-  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "step_pull");
+  return e == cudaSuccess ? debug_check(c) : cuda_fail(c, e, "step_pull");
 }
 
 namespace {
 lbm_status adjoint_ok(lbm_ctx* c) {
   if (c->p.pattern != LBM_PULL) {
-    c->err = "the adjoint works on the two-array pull layout";
+    set_err(c, "the adjoint works on the two-array pull layout");
     return LBM_E_STATE;
   }
   if (c->p.collision == LBM_CUMULANT || c->p.collision == LBM_KBC) {
-    c->err = "the cumulant and KBC operators have no adjoint";
+    set_err(c, "the cumulant and KBC operators have no adjoint");
     return LBM_E_UNSUPPORTED;
   }
   if (c->link_types & L_OUTLET) {
-    c->err = "outlet links are not differentiated";
+    set_err(c, "outlet links are not differentiated");
     return LBM_E_UNSUPPORTED;
   }
   if (c->cp.smag) {
-    c->err = "the Smagorinsky model is not differentiated";
+    set_err(c, "the Smagorinsky model is not differentiated");
     return LBM_E_UNSUPPORTED;
   }
   if (c->p.boundary_mode == LBM_BOUNDARY_SEPARATE) {
-    c->err = "the adjoint works with boundary links resolved in the sweep";
+    set_err(c, "the adjoint works with boundary links resolved in the sweep");
     return LBM_E_UNSUPPORTED;
   }
   return LBM_OK;
@@ -750,7 +810,9 @@ const char* lbm_status_str(lbm_status s) {
   return kStatusNames[(int)s];
 }
 
-const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : ""; }
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : ""; }
+
+void lbm_debug_fail_host_allocs(int32_t n) { g_fail_allocs.store(n > 0 ? n : 0); }
 
 void lbm_destroy(lbm_ctx* c) { delete c; }
 

@@ -88,7 +88,48 @@ struct SweepArgs {
   // reads (lf: fluid link, lb: boundary link) and writes (sf, sb: fluid or
   // boundary link (x, qbar)); unsigned, added modulo 2^32
   unsigned lf[27], lb[27], sf[27], sb[27];
+  // bounds-checking build (LBM_DEBUG_BOUNDS): bytes of each population array
+  // and the device word that records an access outside src or dst
+  size_t pdf_bytes;
+  unsigned* bounds_flag;
 };
+
+// Every population access of the sweep kernels goes through pdf_ld/pdf_st.
+// Built with LBM_DEBUG_BOUNDS they check the address against the src and dst
+// arrays and, outside both, record it in *bounds_flag and skip the access
+// (a load returns zero) instead of trapping; the synchronising calls of the
+// API then return LBM_E_BOUNDS.  Otherwise they are plain accesses.
+template <class V>
+__device__ __forceinline__ bool pdf_in_bounds(const SweepArgs& a, const void* p) {
+  const char* c = static_cast<const char*>(p);
+  const char* s = static_cast<const char*>(a.src);
+  const char* d = static_cast<const char*>(a.dst);
+  const bool in_s = s && c >= s && c + sizeof(V) <= s + a.pdf_bytes;
+  const bool in_d = d && c >= d && c + sizeof(V) <= d + a.pdf_bytes;
+  return in_s || in_d;
+}
+template <class V>
+__device__ __forceinline__ V pdf_ld(const SweepArgs& a, const void* base, long long idx) {
+  const V* p = static_cast<const V*>(base) + idx;
+#ifdef LBM_DEBUG_BOUNDS
+  if (!pdf_in_bounds<V>(a, p)) {
+    atomicOr(a.bounds_flag, 1u);
+    return V();
+  }
+#endif
+  return *p;
+}
+template <class V>
+__device__ __forceinline__ void pdf_st(const SweepArgs& a, void* base, long long idx, V v) {
+  V* p = static_cast<V*>(base) + idx;
+#ifdef LBM_DEBUG_BOUNDS
+  if (!pdf_in_bounds<V>(a, p)) {
+    atomicOr(a.bounds_flag, 1u);
+    return;
+  }
+#endif
+  *p = v;
+}
 
 constexpr int kBlockX = 128;
 
@@ -311,18 +352,18 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
       const int ip = cell - (x == a.g.nx - 1 ? a.g.nx : 0);  // location x + 1 with the x wrap
 #pragma unroll
       for (int q = 0; q < L::Q; ++q)
-        v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[eso_rd(L::cx(q)) ? ip : cell], L::w(q));
+        v[q] = D::load(pdf_ld<S>(a, a.srci[q], eso_rd(L::cx(q)) ? ip : cell), L::w(q));
     } else {
 #pragma unroll
       for (int q = 0; q < L::Q; ++q) {
         const int qs = KIND == K_ESO_EVEN ? q : opp(q);
         const int idx = nb.at(eso_rd(L::cx(q)), eso_rd(L::cy(q)), eso_rd(L::cz(q)));
-        v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
+        v[q] = D::load(pdf_ld<S>(a, a.srcq[qs], idx), L::w(q));
       }
     }
   } else if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) v[q] = D::load(reinterpret_cast<const S*>(a.srcq[q])[cell], L::w(q));
+    for (int q = 0; q < L::Q; ++q) v[q] = D::load(pdf_ld<S>(a, a.srcq[q], cell), L::w(q));
   } else if (fast) {
     // x - c_q with the x wrap: c_x = +1 reads x - 1 (wraps at x = 0), c_x = -1 reads x + 1
     const int im = cell + (x == 0 ? a.g.nx : 0);
@@ -330,14 +371,14 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) {
       const int idx = L::cx(q) > 0 ? im : (L::cx(q) < 0 ? ip : cell);
-      v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[idx], L::w(q));
+      v[q] = D::load(pdf_ld<S>(a, a.srci[q], idx), L::w(q));
     }
   } else {
     // pull: P_q(x - c_q) = src[q][x - c_q];  AA odd: A[qbar][x - c_q]
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) {
       const int qs = KIND == K_PULL ? q : opp(q);
-      v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[nb.at(-L::cx(q), -L::cy(q), -L::cz(q))], L::w(q));
+      v[q] = D::load(pdf_ld<S>(a, a.srcq[qs], nb.at(-L::cx(q), -L::cy(q), -L::cz(q))), L::w(q));
     }
   }
 
@@ -345,10 +386,10 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
 
   if constexpr (KIND == K_PULL) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = D::store(v[q], L::w(q));
+    for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[q], cell, D::store(v[q], L::w(q)));
   } else if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
+    for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[opp(q)], cell, D::store(v[q], L::w(q)));
   } else {
     // The store offsets are rebuilt from a fresh read of %tid.x: an asm with
     // side effects is not moved above the loads and its result cannot be
@@ -365,7 +406,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
 #pragma unroll
       for (int q = 0; q < L::Q; ++q) {
         const int idx = ESO ? (eso_wr(L::cx(q)) ? ip : cs) : (L::cx(q) > 0 ? ip : (L::cx(q) < 0 ? im : cs));
-        reinterpret_cast<S*>(a.dsti[q])[idx] = D::store(v[q], L::w(q));
+        pdf_st<S>(a, a.dsti[q], idx, D::store(v[q], L::w(q)));
       }
     } else {
       const Nbr nbs = make_nbr(a.g, xs, y, z);
@@ -375,7 +416,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
         const int qd = KIND == K_ESO_EVEN ? opp(q) : q;
         const int idx = ESO ? nbs.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)))
                             : nbs.at(L::cx(q), L::cy(q), L::cz(q));
-        reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+        pdf_st<S>(a, a.dstq[qd], idx, D::store(v[q], L::w(q)));
       }
     }
   }
@@ -517,7 +558,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
         qs = KIND == K_PULL ? (b ? opp(q) : q) : (b ? q : opp(q));
         idx = b ? cell : nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
       }
-      v[q] = D::load(reinterpret_cast<const S*>(a.srcq[qs])[idx], L::w(q));
+      v[q] = D::load(pdf_ld<S>(a, a.srcq[qs], idx), L::w(q));
     }
   } else {
     // The two slots a direction can touch, q and qbar, are adjacent streams:
@@ -528,15 +569,15 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
     for (int q = 0; q < L::Q; ++q) {
       const bool b = (mask >> q) & 1u;
       if constexpr (ESO) {
-        v[q] = D::load(reinterpret_cast<const S*>(a.srci[q])[cell], L::w(q));
+        v[q] = D::load(pdf_ld<S>(a, a.srci[q], cell), L::w(q));
       } else if constexpr (KIND == K_AA_EVEN) {
-        v[q] = D::load(reinterpret_cast<const S*>(a.srcq[q])[cell], L::w(q));
+        v[q] = D::load(pdf_ld<S>(a, a.srcq[q], cell), L::w(q));
       } else {
         // pull: fluid src[q][x - c_q], boundary src[qbar][x];
         // AA odd: fluid A[qbar][x - c_q], boundary A[q][x]
         const int lo = q < opp(q) ? q : opp(q);
         const unsigned idx = unsigned(cell) + (b ? a.lb[q] : a.lf[q]);
-        v[q] = D::load(reinterpret_cast<const S*>(a.srcq[lo])[idx], L::w(q));
+        v[q] = D::load(pdf_ld<S>(a, a.srcq[lo], idx), L::w(q));
       }
     }
   }
@@ -580,10 +621,10 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
   }
   if constexpr (KIND == K_PULL) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = D::store(v[q], L::w(q));
+    for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[q], cell, D::store(v[q], L::w(q)));
   } else if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[opp(q)])[cell] = D::store(v[q], L::w(q));
+    for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[opp(q)], cell, D::store(v[q], L::w(q)));
   } else if constexpr (WRAP) {
     int x, y, z;
     cell_coords(a.g, cell, x, y, z);
@@ -603,7 +644,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
         qd = b ? p : q;
         idx = b ? cell : nbs.at(L::cx(q), L::cy(q), L::cz(q));
       }
-      reinterpret_cast<S*>(a.dstq[qd])[idx] = D::store(v[q], L::w(q));
+      pdf_st<S>(a, a.dstq[qd], idx, D::store(v[q], L::w(q)));
     }
   } else {
     // cell and mask are read again (cache hits) rather than held across the
@@ -621,7 +662,7 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
       const bool b = (ms >> p) & 1u;
       const int lo = q < p ? q : p;
       const unsigned idx = unsigned(cs) + (b ? a.sb[q] : a.sf[q]);
-      reinterpret_cast<S*>(a.dstq[lo])[idx] = D::store(v[q], L::w(q));
+      pdf_st<S>(a, a.dstq[lo], idx, D::store(v[q], L::w(q)));
     }
   }
 }
@@ -650,14 +691,15 @@ __global__ void __launch_bounds__(kBlockX) k_boundary_pull(const SweepArgs a, ty
     const Nbr nb = make_nbr(a.g, x, y, z);
 #pragma unroll
     for (int q = 1; q < L::Q; ++q)
-      if ((mask >> q) & 1u) P[q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q))] = P[opp(q) * N + cell];
+      if ((mask >> q) & 1u)
+        pdf_st<S>(a, P, q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q)), pdf_ld<S>(a, P, opp(q) * N + cell));
     return;
   }
   T up[3] = {T(0), T(0), T(0)};
   {
     T v[L::Q];
 #pragma unroll
-    for (int k = 0; k < L::Q; ++k) v[k] = D::load(P[k * N + cell], L::w(k));
+    for (int k = 0; k < L::Q; ++k) v[k] = D::load(pdf_ld<S>(a, P, k * N + cell), L::w(k));
     post_velocity<L, T, DH>(v, outlet_params(a.cp), up);
   }
   const Nbr nb = make_nbr(a.g, x, y, z);
@@ -665,10 +707,11 @@ __global__ void __launch_bounds__(kBlockX) k_boundary_pull(const SweepArgs a, ty
   for (int q = 1; q < L::Q; ++q) {
     if (!((mask >> q) & 1u)) continue;
     const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
-    S* slot = P + q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
-    if (t == L_OUTLET) *slot = D::store(outlet_value<L, T, DH>(q, up, outlet_params(a.cp)), L::w(q));
-    else if (t == L_INLET) *slot = D::store(D::load(P[opp(q) * N + cell], L::w(q)) + ubb_term<L, T>(q, a.cp), L::w(q));
-    else *slot = P[opp(q) * N + cell];  // no-slip: the stored value itself
+    const long long slot = q * N + nb.at(-L::cx(q), -L::cy(q), -L::cz(q));
+    const S own = pdf_ld<S>(a, P, opp(q) * N + cell);
+    if (t == L_OUTLET) pdf_st<S>(a, P, slot, D::store(outlet_value<L, T, DH>(q, up, outlet_params(a.cp)), L::w(q)));
+    else if (t == L_INLET) pdf_st<S>(a, P, slot, D::store(D::load(own, L::w(q)) + ubb_term<L, T>(q, a.cp), L::w(q)));
+    else pdf_st<S>(a, P, slot, own);  // no-slip: the stored value itself
   }
 }
 
@@ -715,8 +758,10 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
       // does cell 0 read x0 - 1 (+1 direction of pull/AA) / cell 1 read x0 + 2?
       const bool lo = ESO ? false : L::cx(q) > 0;
       const bool hi = ESO ? eso_rd(L::cx(q)) != 0 : L::cx(q) < 0;
-      if (!lo && !hi) P[q] = *reinterpret_cast<const __half2*>(base + cell);
-      else P[q] = __halves2half2(base[cell + (lo ? wa : 0)], base[cell + 1 - (hi ? wb : 0)]);
+      if (!lo && !hi) P[q] = pdf_ld<__half2>(a, base + cell, 0);
+      else
+        P[q] = __halves2half2(pdf_ld<__half>(a, base, cell + (lo ? wa : 0)),
+                              pdf_ld<__half>(a, base, cell + 1 - (hi ? wb : 0)));
     }
   }
   if (!fast) {
@@ -727,17 +772,17 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
     const int qs = (KIND == K_AA_ODD || KIND == K_ESO_ODD) ? opp(q) : q;
     const __half* base = reinterpret_cast<const __half*>(a.srcq[qs]);
     if constexpr (KIND == K_AA_EVEN) {
-      P[q] = *reinterpret_cast<const __half2*>(base + cell);
+      P[q] = pdf_ld<__half2>(a, base + cell, 0);
     } else if constexpr (ESO) {
       // location x + max(-c_q, 0): x0 and x0 + 1, or x0 + 1 and x0 + 2
       const int row = yo[eso_rd(L::cy(q)) + 1] + zo[eso_rd(L::cz(q)) + 1];
-      if (eso_rd(L::cx(q)) == 0) P[q] = *reinterpret_cast<const __half2*>(base + row + x0);
-      else P[q] = __halves2half2(base[row + xb[1]], base[row + xb[2]]);
+      if (eso_rd(L::cx(q)) == 0) P[q] = pdf_ld<__half2>(a, base + row + x0, 0);
+      else P[q] = __halves2half2(pdf_ld<__half>(a, base, row + xb[1]), pdf_ld<__half>(a, base, row + xb[2]));
     } else {
       const int dx = -L::cx(q), dy = -L::cy(q), dz = -L::cz(q);
       const int row = yo[dy + 1] + zo[dz + 1];
-      if (dx == 0) P[q] = *reinterpret_cast<const __half2*>(base + row + x0);
-      else P[q] = __halves2half2(base[row + xa[dx + 1]], base[row + xb[dx + 1]]);
+      if (dx == 0) P[q] = pdf_ld<__half2>(a, base + row + x0, 0);
+      else P[q] = __halves2half2(pdf_ld<__half>(a, base, row + xa[dx + 1]), pdf_ld<__half>(a, base, row + xb[dx + 1]));
     }
   }
   }
@@ -755,11 +800,11 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
   for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__low2half(P[q]), __float2half_rn(v[q]));
   if constexpr (KIND == K_PULL) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.dstq[q]) + cell) = P[q];
+    for (int q = 0; q < L::Q; ++q) pdf_st<__half2>(a, reinterpret_cast<__half*>(a.dstq[q]) + cell, 0, P[q]);
   } else if constexpr (KIND == K_AA_EVEN) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q)
-      *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.dstq[opp(q)]) + cell) = P[q];
+      pdf_st<__half2>(a, reinterpret_cast<__half*>(a.dstq[opp(q)]) + cell, 0, P[q]);
   } else if (fast) {
     // writes through the pre-shifted bases (SweepArgs::dsti): cell 0 writes
     // x0 - 1 (wraps at x0 = 0), cell 1 writes x0 + 2 (wraps at x0 + 2 = nx)
@@ -774,10 +819,10 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
       const bool lo = ESO ? false : L::cx(q) < 0;
       const bool hi = ESO ? eso_wr(L::cx(q)) != 0 : L::cx(q) > 0;
       if (!lo && !hi) {
-        *reinterpret_cast<__half2*>(base + c1) = P[q];
+        pdf_st<__half2>(a, base + c1, 0, P[q]);
       } else {
-        base[c1 + (lo ? wa : 0)] = __low2half(P[q]);
-        base[c1 + 1 - (hi ? wb : 0)] = __high2half(P[q]);
+        pdf_st<__half>(a, base, c1 + (lo ? wa : 0), __low2half(P[q]));
+        pdf_st<__half>(a, base, c1 + 1 - (hi ? wb : 0), __high2half(P[q]));
       }
     }
   } else if constexpr (ESO) {
@@ -793,10 +838,10 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
       __half* base = reinterpret_cast<__half*>(a.dstq[KIND == K_ESO_EVEN ? opp(q) : q]);
       const int row = yo2[eso_wr(L::cy(q)) + 1] + zo2[eso_wr(L::cz(q)) + 1];
       if (eso_wr(L::cx(q)) == 0) {
-        *reinterpret_cast<__half2*>(base + row + x1) = P[q];
+        pdf_st<__half2>(a, base + row + x1, 0, P[q]);
       } else {
-        base[row + xb1] = __low2half(P[q]);
-        base[row + xb2] = __high2half(P[q]);
+        pdf_st<__half>(a, base, row + xb1, __low2half(P[q]));
+        pdf_st<__half>(a, base, row + xb2, __high2half(P[q]));
       }
     }
   } else {
@@ -814,10 +859,10 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
       const int dx = L::cx(q), dy = L::cy(q), dz = L::cz(q);
       const int row = yo2[dy + 1] + zo2[dz + 1];
       if (dx == 0) {
-        *reinterpret_cast<__half2*>(base + row + x1) = P[q];
+        pdf_st<__half2>(a, base + row + x1, 0, P[q]);
       } else {
-        base[row + xa2[dx + 1]] = __low2half(P[q]);
-        base[row + xb2[dx + 1]] = __high2half(P[q]);
+        pdf_st<__half>(a, base, row + xa2[dx + 1], __low2half(P[q]));
+        pdf_st<__half>(a, base, row + xb2[dx + 1], __high2half(P[q]));
       }
     }
   }
@@ -1132,7 +1177,7 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int la
   if (layout == 2 && (mask & MASK_SOLID)) return;
   if (layout == 0 || (mask & MASK_SOLID)) {
 #pragma unroll
-    for (int q = 0; q < L::Q; ++q) reinterpret_cast<S*>(a.dstq[q])[cell] = ST::from_h(v[q], L::w(q));
+    for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[q], cell, ST::from_h(v[q], L::w(q)));
     return;
   }
   if constexpr (BND) {
@@ -1158,7 +1203,7 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int la
       const int p = opp(q);
       const bool b = BND && ((mask >> p) & 1u);
       const int idx = nb.at(eso_wr(L::cx(q)), eso_wr(L::cy(q)), eso_wr(L::cz(q)));
-      reinterpret_cast<S*>(a.dstq[b ? p : q])[idx] = ST::from_h(v[q], L::w(q));
+      pdf_st<S>(a, a.dstq[b ? p : q], idx, ST::from_h(v[q], L::w(q)));
     }
     return;
   }
@@ -1168,7 +1213,7 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int la
     const bool b = BND && ((mask >> p) & 1u);
     const int qd = b ? p : q;
     const int idx = b ? cell : nb.at(L::cx(q), L::cy(q), L::cz(q));
-    reinterpret_cast<S*>(a.dstq[qd])[idx] = ST::from_h(v[q], L::w(q));
+    pdf_st<S>(a, a.dstq[qd], idx, ST::from_h(v[q], L::w(q)));
   }
 }
 

@@ -105,3 +105,21 @@ def test_stencil_table_matches_documented_order(L, name):
     assert q == ref.q and d == ref.d
     assert [tuple(v[:d]) for v in c] == ref.c_list
     assert np.allclose(w, ref.w, rtol=0, atol=1e-17)
+
+
+def test_injected_host_allocation_failure(L):
+    """lbm_create reports a failed host allocation as LBM_E_NOMEM and leaves
+    nothing behind; the next create succeeds.  A periodic box without flags
+    makes no CUDA call at create time, so fake device pointers suffice."""
+    p = _params(nx=4, ny=4, nz=4)
+    ctx = ctypes.c_void_p()
+    s, pdf, aux = _query(p)
+    fake = 0x1000
+    L.lbm_debug_fail_host_allocs(1)
+    assert L.lbm_create(ctypes.byref(ctx), ctypes.byref(p), fake, pdf, fake, pdf, fake, aux, None, None) == 4
+    assert not ctx.value
+    assert L.lbm_create(ctypes.byref(ctx), ctypes.byref(p), fake, pdf, fake, pdf, fake, aux, None, None) == 0
+    assert ctx.value
+    assert L.lbm_last_error(ctx) == b""
+    L.lbm_destroy(ctx)
+    L.lbm_debug_fail_host_allocs(0)

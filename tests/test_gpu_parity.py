@@ -537,3 +537,50 @@ def test_separate_boundary_kernel_needs_closed_faces():
     buf = torch.zeros((19, sim.N), dtype=torch.float64, device=sim.device)
     out = torch.zeros_like(buf)
     assert _lib.lib().lbm_adjoint_step(sim.ctx, sim.pdf.data_ptr(), buf.data_ptr(), out.data_ptr(), None) == 2
+
+
+def test_nonfinite_state_is_reported_and_context_stays_usable():
+    """A NaN in the populations reaches the FP64 reduction, which returns
+    LBM_E_NONFINITE; the context keeps working after a new state is set."""
+    from paper_2001_11806_gb300 import LbmError
+    lat = olat.d3q19()
+    shape = (12, 6, 5)
+    P = inputs.random_pdfs(lat.w, shape[::-1], seed=41).reshape(19, -1)
+    sim = Sim("D3Q19", "trt", "f32", "aa", shape, omega=[1.6, 1.1])
+    bad = P.copy()
+    bad[3, 17] = np.nan
+    sim.set_state(bad)
+    sim.step(2)
+    with pytest.raises(LbmError) as e:
+        sim.reduce()
+    assert e.value.status == 6
+    assert b"non-finite" in _lib_last_error(sim)
+    sim.set_state(P)
+    sim.step(2)
+    assert np.all(np.isfinite(sim.reduce()))
+
+
+def test_injected_allocation_failure_with_flags():
+    """A context with a flag field allocates the host offsets of its
+    fluid-cell list; an injected failure there returns LBM_E_NOMEM."""
+    from paper_2001_11806_gb300 import LbmError, _lib
+    fl = _flags(_shape("D3Q19", big=False))
+    _lib.lib().lbm_debug_fail_host_allocs(2)  # the context, then the list offsets
+    try:
+        with pytest.raises(LbmError) as e:
+            Sim("D3Q19", "trt", "f32", "pull", _shape("D3Q19", big=False), periodic=(False, False, True),
+                omega=[1.6, 1.1], flags=fl)
+        assert e.value.status == 4
+        with pytest.raises(LbmError) as e:
+            Sim("D3Q19", "trt", "f32", "pull", _shape("D3Q19", big=False), periodic=(False, False, True),
+                omega=[1.6, 1.1], flags=fl)
+        assert e.value.status == 4
+    finally:
+        _lib.lib().lbm_debug_fail_host_allocs(0)
+    Sim("D3Q19", "trt", "f32", "pull", _shape("D3Q19", big=False), periodic=(False, False, True),
+        omega=[1.6, 1.1], flags=fl).close()
+
+
+def _lib_last_error(sim):
+    from paper_2001_11806_gb300 import _lib
+    return _lib.lib().lbm_last_error(sim.ctx)

@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kListThreads) k_list_scatter(const SweepArgs a
 // (WRAP = true: neighbour indices from the coordinates, with wrapping, and the
 // inlet/outlet fix-ups).
 template <class L, class ST, int OP, int KIND, bool WRAP>
-__global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
+__device__ __forceinline__ void sweep_list(const SweepArgs& a) {
   using T = typename ST::T;
   using S = typename ST::S;
   constexpr bool DH = dom_h<ST, OP>();
@@ -665,6 +665,37 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
       pdf_st<S>(a, a.dstq[lo], idx, D::store(v[q], L::w(q)));
     }
   }
+}
+
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
+  sweep_list<L, ST, OP, KIND, false>(a);
+}
+
+// The main list sweep of D3Q19 with 16-bit storage under SRT, TRT and
+// one-higher-rate MRT, with a register cap.  Each thread waits on two
+// dependent loads (list entry, then link mask) before its population loads
+// can issue, and with 2-byte populations it moves half the bytes per load,
+// so it needs more warps in flight per SM than the 32-bit sweep to keep the
+// bytes in flight that hide the latency; the cap trades a few values spilled
+// to L1 for those warps (with 32-bit storage the same cap was slower).
+#ifndef LBM_LIST_MAXNREG
+#define LBM_LIST_MAXNREG 48
+#endif
+
+template <class L, class ST, int OP>
+constexpr bool list_capped() {
+  return L::Q == 19 && sizeof(typename ST::S) == 2 && (OP == OP_SRT || OP == OP_TRT || OP == OP_MRT3);
+}
+
+template <class L, class ST, int OP, int KIND>
+__global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArgs a) {
+  sweep_list<L, ST, OP, KIND, false>(a);
+}
+
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX) k_sweep_list_wrap(const SweepArgs a) {
+  sweep_list<L, ST, OP, KIND, true>(a);
 }
 
 // Separate boundary kernel of the two-grid pull (LBM_BOUNDARY_SEPARATE):
@@ -1241,10 +1272,16 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
     k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
     return cudaGetLastError();
   }
-  if (a.n_main > 0) k_sweep_list<L, ST, OP, KIND, false><<<(a.n_main + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(a);
+  if (a.n_main > 0) {
+    const int nb = (a.n_main + kBlockX - 1) / kBlockX;
+    if constexpr (list_capped<L, ST, OP>())
+      k_sweep_list_capped<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(a);
+    else
+      k_sweep_list<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.n_wrap > 0) k_sweep_list<L, ST, OP, KIND, true><<<(a.n_wrap + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(a);
+  if (a.n_wrap > 0) k_sweep_list_wrap<L, ST, OP, KIND><<<(a.n_wrap + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(a);
   return cudaGetLastError();
 }
 

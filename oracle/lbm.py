@@ -17,7 +17,11 @@ the flag of the source cell with precedence NOSLIP > INLET > OUTLET:
   direction c_qbar and rho_0 = 1): B_q = P_qbar(x) - 2 w_q (c_qbar.u_w)/cs2.
 - OUTLET (not in the paper; reading): B_q = f^eq_q(rho_out, u_P(x)) with
   u_P = (sum_q c_q P_q - F/2) / rho_0(P) the velocity of the cell's own last
-  collision.  "parity unpinned": only oracle-vs-GPU agreement checks it.
+  collision.  Pinned by what a velocity inlet and a pressure outlet must
+  produce in a channel periodic across the flow (tests/test_oracle_outlet.py):
+  the uniform state rho = rho_out, j = rho_0 u_in is a fixed point, and the
+  steady state reached from rest.  Which velocity it takes in a transient is
+  the reading, which only oracle-vs-GPU agreement checks.
 
 Output.  ``populations`` returns f(x) (the pre-collision populations the next
 step would collide); ``macroscopic`` returns their moments (Eq. density, with
@@ -29,7 +33,8 @@ or OUTLET link and bit 31 for non-fluid cells.
 Pins: tests/test_oracle_lbm.py (pull streaming against an independent
 np.roll shift, global mass conservation with walls, bounce-back reversing a
 free-streaming packet, UBB momentum input, mask bits against a brute-force
-loop) and tests/test_oracle_flows.py (TGV decay, Poiseuille parabola).
+loop), tests/test_oracle_outlet.py (inlet/outlet fixed point and steady
+state) and tests/test_oracle_flows.py (TGV decay, Poiseuille parabola).
 """
 import numpy as np
 

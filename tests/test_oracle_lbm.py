@@ -140,3 +140,18 @@ def test_link_mask_brute_force():
                     if 0 <= sy < 5 and flags[sz, sy, sx] in (lbm.INLET, lbm.OUTLET):
                         ref |= 1 << 30
         assert mask[z, y, x] == ref, (z, y, x)
+
+
+def test_link_kind_of_every_flag_value():
+    # the documented rule for a uint8 flag: 0 is fluid; otherwise NOSLIP if
+    # bit 0 is set or no known bit is set, else INLET if bit 1, else OUTLET
+    for v in range(256):
+        if v == 0:
+            want = lbm.FLUID
+        elif v & 1 or not v & 6:
+            want = lbm.NOSLIP
+        elif v & 2:
+            want = lbm.INLET
+        else:
+            want = lbm.OUTLET
+        assert lbm.link_kind(np.uint8(v)) == want, v

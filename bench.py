@@ -52,6 +52,18 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def algorithmic_bytes(q, value_bytes, fluid_cells, mask_cells=0):
+    """Bytes one stream-collide step must move (Sec. V: read and write every
+    population once, 2 q values per fluid cell), plus the 4-byte link mask of
+    every cell of a masked domain."""
+    return 2 * q * value_bytes * fluid_cells + 4 * mask_cells
+
+
+def roofline_mlups(bandwidth_gbs, q, value_bytes):
+    """Memory-bound MLUPS limit: bandwidth / bytes per cell update."""
+    return bandwidth_gbs * 1e9 / algorithmic_bytes(q, value_bytes, 1) / 1e6
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_2001_11806_gb300", "csrc", "*"))):
@@ -304,7 +316,7 @@ def run_variants(device, peak, only=None, steps_override=None, warmup=10):
         sim.step(warmup)
         ms = _time_steps(sim, steps, torch)
         fluid = N if flags is None else int((flags == 0).sum())
-        nbytes = 2 * q * elem[kw["storage"]] * fluid + (4 * N if flags is not None else 0)
+        nbytes = algorithmic_bytes(q, elem[kw["storage"]], fluid, N if flags is not None else 0)
         gbs = nbytes / (ms * 1e-3) / 1e9
         out.append({"workload": name, "mlups": round(N / ms / 1e3, 1),
                     "fluid_mlups": round(fluid / ms / 1e3, 1), "ms_per_step": round(ms, 4),
@@ -498,7 +510,7 @@ def run_gpu(args, world, rank, local):
     if rank != 0:
         return 0
     peak, peak_kind = measured_peak()
-    bytes_per_launch = 2 * Q * ELEM * cells
+    bytes_per_launch = algorithmic_bytes(Q, ELEM, cells)
     if n != N_SIDE:
         line_workload = WORKLOAD.replace("256^3", f"{n}^3")
     else:

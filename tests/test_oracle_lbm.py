@@ -155,3 +155,23 @@ def test_link_kind_of_every_flag_value():
         else:
             want = lbm.OUTLET
         assert lbm.link_kind(np.uint8(v)) == want, v
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_ubb_at_rest_is_bounce_back(name):
+    # the UBB listing with wall velocity 0 adds nothing: an inlet at rest
+    # must give exactly the populations of a no-slip wall
+    lat = lattice.get(name)
+    shp = _shape(lat, (6, 5, 3))
+    P = inputs.random_pdfs(lat.w, shp[::-1], seed=12)
+    out = []
+    for kind in (lbm.INLET, lbm.NOSLIP):
+        flags = np.zeros(shp[::-1], np.uint8)
+        flags[:, 0, :] = kind
+        flags[:, -1, :] = lbm.NOSLIP
+        s = lbm.Sim(co.Method(lat, "trt", [1.3, 0.9]), shp, periodic=(True, False, True), flags=flags,
+                    u_wall=(0.0, 0.0, 0.0))
+        s.P = P.copy()
+        s.step(3)
+        out.append(s.populations())
+    assert np.array_equal(out[0], out[1])

@@ -175,3 +175,20 @@ def test_gradient_against_central_differences(monkeypatch):
         e[a] = h
         fd = (_direct(model, u0, F + e, T)[0] - _direct(model, u0, F - e, T)[0]) / (2 * h)
         assert abs(fd - float(g_F.numpy()[a])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_autograd_function_routes_the_gradients(monkeypatch):
+    model = Model(seed=5)
+    T = 7
+    rng = np.random.default_rng(2)
+    u0_np = 0.1 * rng.standard_normal((D, NC))
+    F_np = np.array([0.01, -0.02, 0.005])
+    r, _ = _rollout(model, T, monkeypatch)
+    u0 = torch.tensor(u0_np, dtype=torch.float64, requires_grad=True)
+    F = torch.tensor(F_np, dtype=torch.float64, requires_grad=True)
+    L = adjoint.LBMRollout.apply(u0, F, r, np.ones(NC))
+    (3.0 * L).backward()
+    L_ref, gu_ref, gF_ref = _direct(model, u0_np, F_np, T)
+    assert abs(float(L.detach()) - L_ref) <= 1e-13 * abs(L_ref)
+    assert np.allclose(u0.grad.numpy().reshape(-1), 3.0 * gu_ref, rtol=1e-12, atol=1e-14)
+    assert np.allclose(F.grad.numpy(), 3.0 * gF_ref, rtol=1e-12, atol=1e-14)

@@ -116,6 +116,14 @@ def max_over_ranks(world, v, device=None):
     return float(t.item())
 
 
+def smi_device_id(local):
+    """nvidia-smi -i id of this rank's GPU: the local-th entry of
+    CUDA_VISIBLE_DEVICES (an index or a UUID, both accepted by -i), else the
+    local rank itself."""
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return vis[local] if local < len(vis) else str(local)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region.
 
@@ -467,8 +475,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize(device)
 
     # ---- device-resident timed region
-    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks = ClockSampler(smi_device_id(local))
     clocks.start()
     barrier(world)
     torch.cuda.synchronize(device)

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, literal restatement
 of the method of Bauer, Koestler & Ruede, "lbmpy: Automatic code generation
 for efficient parallel lattice Boltzmann methods" (arXiv:2001.11806), used to
 check the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import it.  The product package never
+CPU-baseline leg and reference arm of ``bench.py`` may import it.  The product package never
 imports it and shares no code, table or constant generator with it.
 
 Everything is numpy float64, vectorised over cells only; per-cell formulas are
@@ -16,7 +16,8 @@ written in the paper's notation.  Modules:
                 (Sec. III-A "Moment Space"), Maxwellian moments (Eqs.
                 cont_maxwellian / cont_moment_integral).
 - ``collision`` equilibrium (Eq. discrete_eq), SRT (Eq. bgk), TRT, MRT
-                (Eq. mrt) and Guo forcing.
+                (Eq. mrt), Guo forcing, the Smagorinsky model (Sec. III-C)
+                and the entropic KBC operator (Eq. entropic_direct_omega_eq).
 - ``cumulant``  cumulant collision from the generating function
                 (Eq. cumulant_generating_function) in a truncated power-series
                 ring.

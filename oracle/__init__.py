@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, literal restatement
 of the method of Bauer, Koestler & Ruede, "lbmpy: Automatic code generation
 for efficient parallel lattice Boltzmann methods" (arXiv:2001.11806), used to
 check the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg and reference arm of ``bench.py`` may import it.  The product package never
-imports it and shares no code, table or constant generator with it.
+CPU-baseline leg and reference arm of ``bench.py`` may import it.  The
+product package never imports it and shares no code, table or constant
+generator with it.
 
 Everything is numpy float64, vectorised over cells only; per-cell formulas are
 written in the paper's notation.  Modules:

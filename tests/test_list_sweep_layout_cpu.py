@@ -72,3 +72,29 @@ def test_plain_cells_pull_through_fixed_offsets(stencil, periodic):
         # every source outside the box is a boundary link, read from the cell itself
         assert (~fl_link[~inside]).all(), q
         assert np.array_equal(src[q, cells[~fl_link]], lat.opp[q] * N + cells[~fl_link]), q
+
+
+@pytest.mark.parametrize("stencil", ["D2Q9", "D3Q19", "D3Q27"])
+def test_dense_inner_rows_pull_through_offsets_with_an_x_correction(stencil):
+    """The periodic sweep's fast path: in a row whose y and z neighbours do
+    not wrap, the source of link (x, q) is the cell index minus the fixed
+    offset, corrected by +-nx where x - c_x wraps."""
+    lat = olat.get(stencil)
+    shape = (9, 6, 1) if lat.d == 2 else (9, 6, 5)
+    s = olbm.Sim(oco.Method(lat, "srt", [1.2]), shape)
+    nx, ny, nz = shape
+    N = s.N
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    X, Y, Z = X.reshape(-1), Y.reshape(-1), Z.reshape(-1)
+    inner = (Y > 0) & (Y < ny - 1)
+    if lat.d == 3:
+        inner &= (Z > 0) & (Z < nz - 1)
+    cells = np.flatnonzero(inner)
+    src = s.src.reshape(lat.q, -1)
+    c3 = np.zeros((lat.q, 3), np.int64)
+    c3[:, : lat.d] = lat.c
+    for q in range(lat.q):
+        off = c3[q, 0] + nx * c3[q, 1] + nx * ny * c3[q, 2]
+        xs = X[cells] - c3[q, 0]
+        corr = np.where(xs < 0, nx, np.where(xs >= nx, -nx, 0))
+        assert np.array_equal(src[q, cells], q * N + cells - off + corr), q

@@ -150,6 +150,12 @@ class Sim:
         return out, self.t
 
     def set_pdfs(self, raw, t):
+        """Restore a state saved by get_pdfs; raw must be a contiguous tensor
+        of exactly pdf_bytes on the device (the C call copies pdf_bytes from
+        it and cannot check its size)."""
+        if not isinstance(raw, torch.Tensor) or not raw.is_contiguous() or \
+                raw.numel() * raw.element_size() != self.pdf_bytes or raw.device.type != self.device.type:
+            raise LbmError(f"set_pdfs needs a contiguous {self.device.type} tensor of {self.pdf_bytes} bytes")
         self._check(lib().lbm_set_pdfs(self.ctx, raw.data_ptr(), int(t)), "set_pdfs")
 
     def sync(self):

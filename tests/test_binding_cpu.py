@@ -6,11 +6,14 @@ field's offset, which must equal ctypes' (a mismatch would pass shifted
 parameters to every call).  (2) ``Sim`` marshals its arguments into that
 struct and the buffer sizes of lbm_query_sizes: lbm_create is intercepted
 (the rest is the real library), the captured call is checked field by
-field, and the intercepted call's error status is raised as LbmError."""
+field, and the intercepted call's error status is raised as LbmError.
+(3) set_pdfs refuses a buffer that is not exactly pdf_bytes before the C
+call, which copies pdf_bytes from whatever pointer it gets."""
 import ctypes
 import os
 import shutil
 import subprocess
+import types
 
 import pytest
 import torch
@@ -133,3 +136,20 @@ def test_sim_rejects_flags_of_the_wrong_size(monkeypatch, L):
         sim_mod.Sim("D3Q19", "srt", "f32", "aa", (4, 4, 4), flags=torch.zeros(10, dtype=torch.uint8).numpy(),
                     device="cpu", stream=_Stream())
     assert fake.call is None
+
+
+def test_set_pdfs_checks_the_buffer_before_the_copy(monkeypatch):
+    # the C call copies pdf_bytes from the pointer it gets; the binding must
+    # refuse anything else before the call
+    calls = []
+    fake = types.SimpleNamespace(lbm_set_pdfs=lambda *a: calls.append(a) or 0)
+    monkeypatch.setattr(sim_mod, "lib", lambda: fake)
+    s = object.__new__(sim_mod.Sim)
+    s.ctx, s.pdf_bytes, s.device = None, 64, torch.device("cpu")
+    for bad in (torch.zeros(63, dtype=torch.uint8), torch.zeros(8, dtype=torch.float32),
+                torch.zeros(128, dtype=torch.uint8)[::2], b"x" * 64):
+        with pytest.raises(_lib.LbmError, match="set_pdfs needs"):
+            s.set_pdfs(bad, 3)
+    assert not calls
+    s.set_pdfs(torch.zeros(16, dtype=torch.float32), 3)  # 64 bytes, contiguous
+    assert len(calls) == 1 and calls[0][2] == 3

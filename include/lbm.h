@@ -153,22 +153,28 @@ typedef struct lbm_params {
 typedef struct lbm_ctx lbm_ctx;
 
 /* Fill *p with defaults: D3Q19 TRT FP32 pull, 1^3 periodic cells, omega 1.0,
- * rho_outlet 1, no force. */
+ * rho_outlet 1, no force.  Interface plumbing (the runtime parameters of
+ * Sec. IV-D), no method step of its own. */
 void lbm_default_params(lbm_params* p);
 
-/* Stencil table: *q, *d, and if non-NULL c[q*3] (integer velocities, unused
+/* Stencil table of the DdQq velocity sets and weights (Sec. III-A, c_s^2 =
+ * 1/3): *q, *d, and if non-NULL c[q*3] (integer velocities, unused
  * components zero) and w[q] (weights).  Returns LBM_E_INVAL for an unknown
  * stencil. */
 lbm_status lbm_stencil_info(int32_t stencil, int32_t* q, int32_t* d, int32_t* c, double* w);
 
-/* Bytes the caller must allocate: pdf_bytes for each population array
- * (q * N * sizeof(storage)); aux_bytes for the auxiliary device buffer
+/* Bytes the caller must allocate (the array layout that Sec. IV-D passes as
+ * shape and stride, q values per cell as counted in Sec. V): pdf_bytes for
+ * each population array (q * N * sizeof(storage)); aux_bytes for the auxiliary device buffer
  * (link mask and fluid-cell list of 4*N bytes each, used when flags or
  * non-periodic axes are present but reserved in every case, the list
  * builder's counts and the reduction scratch).  Validates p. */
 lbm_status lbm_query_sizes(const lbm_params* p, size_t* pdf_bytes, size_t* aux_bytes);
 
-/* Create a context over caller-owned device buffers.
+/* Create a context over caller-owned device buffers (Sec. IV-D "Framework
+ * Integration": each generated kernel takes raw array pointers, the shape
+ * that fixes their layout, and the method's free symbols, relaxation rates
+ * and forces, as runtime parameters; here they are gathered once in p).
  *   pdf, pdf2: population arrays of pdf_bytes each; pdf2 must be non-NULL for
  *     LBM_PULL and is ignored (may be NULL) for LBM_AA and LBM_ESOTWIST.
  *   aux: auxiliary device buffer of aux_bytes.
@@ -181,26 +187,34 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
                       void* pdf2, size_t pdf2_bytes, void* aux, size_t aux_bytes,
                       const uint8_t* flags, void* stream);
 
-/* Change the stream later calls enqueue on. */
+/* Change the stream later calls enqueue on (interface plumbing, no method
+ * step; the paper's GPU kernels run on pycuda streams, Sec. IV-D). */
 lbm_status lbm_set_stream(lbm_ctx* ctx, void* stream);
 
-/* Set P = f^eq(rho_0, u_0) (Eq. discrete_eq) from device FP64 arrays
+/* Set P = f^eq(rho_0, u_0) (Eq. discrete_eq, second order) from device FP64 arrays
  * rho[N] and u[d][N]; resets the step counter to 0. */
 lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* u);
 
-/* Set P from a device FP64 array P[q][N] (unshifted populations); resets
- * the step counter to 0. */
+/* Set P from a device FP64 array P[q][N] (unshifted populations), written
+ * in the pattern's layout (Sec. IV-B "Streaming and Collision"); resets the
+ * step counter to 0. */
 lbm_status lbm_set_state(lbm_ctx* ctx, const double* P);
 
-/* Advance n >= 0 time steps (asynchronous). */
+/* Advance n >= 0 time steps (asynchronous).  One step is the fused
+ * stream-collide sweep of Sec. IV-B "Streaming and Collision" in the
+ * configured pattern (two-array pull, AA or esoteric twist), with the
+ * boundary links of Sec. IV-B "Boundary Conditions" resolved in the sweep
+ * or, for LBM_BOUNDARY_SEPARATE, by a boundary kernel run before it. */
 lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
 
 /* Number of steps since the last initialisation (AA and esoteric-twist parity
- * = t mod 2). */
+ * = t mod 2, Sec. IV-B "Streaming and Collision": the single-array patterns
+ * alternate between an even and an odd kernel). */
 lbm_status lbm_get_time(const lbm_ctx* ctx, int64_t* t);
 
 /* Populations f of the current time (streamed, pre-collision, unshifted) as
- * device FP64 f[q][N]; non-fluid cells are written as NaN. */
+ * device FP64 f[q][N], read through the pattern's current parity (Sec. IV-B
+ * "Streaming and Collision"); non-fluid cells are written as NaN. */
 lbm_status lbm_populations(lbm_ctx* ctx, double* f);
 
 /* rho[N] and u[d][N] (device, FP64 if out_f64 else FP32) from the current
@@ -210,30 +224,41 @@ lbm_status lbm_macroscopic(lbm_ctx* ctx, void* rho, void* u, int32_t out_f64);
 
 /* FP64 sums over fluid cells: out[0] = sum rho, out[1..3] = sum rho_0 u,
  * out[4] = (1/2) sum rho |u|^2.  Host array out[5].  Synchronises the
- * stream.  Returns LBM_E_NONFINITE if any sum is NaN or Inf. */
+ * stream.  Returns LBM_E_NONFINITE if any sum is NaN or Inf.  Not in the
+ * paper: a conservation check built on its statement that collisions
+ * conserve mass and momentum (Sec. III-A, the conserved moments of rate 0),
+ * with moments as in Eq. density. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double out[5]);
 
 /* Raw copy of the native population storage (pdf_bytes, device to device),
  * for checkpoint/restore.  lbm_set_pdfs also sets the step counter to t so
- * that the AA or esoteric-twist parity matches the saved data. */
+ * that the AA or esoteric-twist parity matches the saved data.  Not in the
+ * paper: the saved layout is the pattern's own (Sec. IV-B "Streaming and
+ * Collision"), so a restore needs the step parity with it. */
 lbm_status lbm_get_pdfs(lbm_ctx* ctx, void* dst);
 lbm_status lbm_set_pdfs(lbm_ctx* ctx, const void* src, int64_t t);
 
 /* Device uint32[N] link mask: bit q set when the source x - c_q of a fluid
  * cell x is not fluid (a boundary link); LBM_MASK_SPECIAL when one of those
  * links is an INLET or OUTLET link; LBM_MASK_SOLID for non-fluid cells.
- * Computed on the device from the flags. */
+ * Computed on the device from the flags.  This is the per-cell form of the
+ * paper's per-link boundary information (Sec. IV-B "Boundary Conditions":
+ * a flag field sets up the boundaries, from which one entry per boundary
+ * link is extracted); exported for bit-exact checks of that extraction. */
 lbm_status lbm_link_mask(lbm_ctx* ctx, uint32_t* mask);
 
-/* Replace the uniform body force (Guo scheme); takes effect for later
- * launches.  LBM_E_UNSUPPORTED for a non-zero force with cumulant or KBC
+/* Replace the uniform body force (Guo scheme, Sec. I; like the paper's
+ * constant external forces it is a runtime parameter of the kernels, Sec.
+ * IV-D); takes effect for later launches.  LBM_E_UNSUPPORTED for a non-zero force with cumulant or KBC
  * collision. */
 lbm_status lbm_set_force(lbm_ctx* ctx, const double F[3]);
 
 /* One time step of the pull pattern from the population array src into dst
- * (both pdf_bytes, distinct; the context's own arrays are not touched).
- * LBM_E_STATE for an AA context, LBM_E_UNSUPPORTED with separate boundary
- * kernels.  Used to recompute checkpoint segments. */
+ * (both pdf_bytes, distinct; the context's own arrays are not touched): the
+ * two-array stream-pull-collide sweep of Sec. IV-B "Streaming and Collision"
+ * on explicit arrays.  LBM_E_STATE for an AA context, LBM_E_UNSUPPORTED with
+ * separate boundary kernels.  Not a separate step of the paper: it exists to
+ * recompute checkpoint segments for the adjoint. */
 lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
 
 /* Discrete adjoint of one pull time step (the paper has no adjoint; this is
@@ -250,7 +275,8 @@ lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* P_prev, const void* lam_in, void* lam_out,
                             double* dLdF);
 
-/* Kinetic energy in a box, L = (1/2) sum rho |u|^2 over the fluid cells with
+/* Not in the paper (the objective of the adjoint): kinetic energy in a box,
+ * L = (1/2) sum rho |u|^2 over the fluid cells with
  * box[0] <= x < box[1], box[2] <= y < box[3], box[4] <= z < box[5], of the
  * populations f = S(P) (u with the Guo half force), ADDED to the device
  * double *L.  If lam_out is non-NULL it receives the adjoint seed
@@ -262,7 +288,9 @@ lbm_status lbm_ke_loss_seed(lbm_ctx* ctx, const void* P, const int32_t box[6], d
 
 /* g_u0 = (d f^eq(rho_0, u_0) / d u_0)^T lam for the initial state written by
  * lbm_init_equilibrium: rho0[N], u0[d][N] and g_u0[d][N] are device FP64, lam
- * as in lbm_adjoint_step.  Non-fluid cells receive zero. */
+ * as in lbm_adjoint_step.  Non-fluid cells receive zero.  Not in the paper:
+ * the transpose of the derivative of Eq. discrete_eq with respect to u,
+ * which closes the adjoint sweep at t = 0. */
 lbm_status lbm_eq_vjp(lbm_ctx* ctx, const double* rho0, const double* u0, const void* lam, double* g_u0);
 
 /* The sums of lbm_reduce without a context and without any allocation, for
@@ -279,21 +307,32 @@ lbm_status lbm_eq_vjp(lbm_ctx* ctx, const double* rho0, const double* u0, const 
  *   out:    device double[5]; receives the same five sums as lbm_reduce;
  *   stream: cudaStream_t (NULL = legacy default stream); the call enqueues work
  *           and returns without synchronising.
- * Scratch lives in a fixed 160 KiB array in the library's device memory that
- * every GPU which loads the library keeps until the process exits.  The first
- * call on each device (with that device current) looks up the array's device
- * address, so make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU race.  Returns LBM_E_INVAL
- * for more than 67,108,864 cells (the cells the fixed scratch covers), and
- * never calls cudaMalloc or cudaFree. */
+ * Scratch lives in a fixed 160 KiB array in the library's device memory.  The
+ * CUDA runtime places it on a device when the library's module is loaded
+ * there, which with lazy module loading (the default of current toolkits) is
+ * the first call on that device, not the loading of the library: that first
+ * call (with the device current) loads the module, places the array and looks
+ * up its device address, so it can itself take 160 KiB of device memory and
+ * fail with LBM_E_CUDA if none is left.  Callers whose allocator reserves the
+ * GPU should therefore make one call at start-up, before the allocator takes
+ * the memory, and before any stream capture.  The array then stays until the
+ * process exits.  Every call shares it: calls that overlap on the GPU race.
+ * The call does not synchronise, so it cannot report a non-finite sum
+ * (lbm_reduce's LBM_E_NONFINITE): a NaN or Inf is left in out, and a caller
+ * using the sums as a conservation check must test out[] after synchronising.
+ * Returns LBM_E_INVAL for more than 67,108,864 cells (the cells the fixed
+ * scratch covers), and never calls cudaMalloc or cudaFree. */
 lbm_status lbm_reduce_noalloc(const lbm_params* p, const void* pdf, const uint8_t* flags, int64_t t,
                               double* out, void* stream);
 
-/* Block until the context's stream is idle; maps pending CUDA errors. */
+/* Block until the context's stream is idle; maps pending CUDA errors
+ * (interface plumbing, no method step). */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
+/* Name of a status code; lbm_last_error: last error message of this context
+ * ("" if none), never NULL.  Error reporting of the interface, no method
+ * step. */
 const char* lbm_status_str(lbm_status s);
-/* Last error message of this context ("" if none); never NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
 /* Test hook for the failure paths (the paper has no counterpart): the next n
@@ -303,6 +342,8 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * clears the request.  Process-wide, not thread-specific. */
 void lbm_debug_fail_host_allocs(int32_t n);
 
+/* Free the context's host metadata; device buffers stay the caller's.
+ * Interface plumbing, no method step. */
 void lbm_destroy(lbm_ctx* ctx);
 
 #ifdef __cplusplus

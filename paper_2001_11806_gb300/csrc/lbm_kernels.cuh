@@ -1127,6 +1127,39 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const SweepArgs 
 // Sum nblocks partial rows into out[5] (one block, fixed order).
 __global__ void k_reduce_final(const double* partials, int nblocks, double* out);
 
+// Boundary links of the fluid cell (x, y, z): bit q is set when its source
+// x - c_q is not fluid (outside a non-periodic axis, or a non-zero flag),
+// MASK_SPECIAL when one of those links is an INLET or OUTLET link; types
+// receives the OR of those links' types.  The link-mask builder and the
+// allocation-free reduction both take a cell's links from here.
+template <class L>
+__device__ __forceinline__ uint32_t cell_links(const Geom& g, const uint8_t* flags, int x, int y, int z,
+                                               unsigned& types) {
+  uint32_t m = 0;
+  types = 0;
+  for (int q = 1; q < L::Q; ++q) {
+    int sx = x - L::cx(q), sy = y - L::cy(q), sz = z - L::cz(q);
+    bool solid = false;
+    if (sx < 0 || sx >= g.nx) { if (!g.per[0]) solid = true; else sx = (sx + g.nx) % g.nx; }
+    if (sy < 0 || sy >= g.ny) { if (!g.per[1]) solid = true; else sy = (sy + g.ny) % g.ny; }
+    if (sz < 0 || sz >= g.nz) { if (!g.per[2]) solid = true; else sz = (sz + g.nz) % g.nz; }
+    int type = L_NOSLIP;
+    if (!solid && flags != nullptr) {
+      const uint8_t f = flags[sx + g.nx * (sy + g.ny * sz)];
+      solid = f != 0;
+      if (solid) type = link_type_of_flag(f);
+    }
+    if (solid) {
+      m |= 1u << q;
+      if (type != L_NOSLIP) {
+        m |= MASK_SPECIAL;
+        types |= unsigned(type);
+      }
+    }
+  }
+  return m;
+}
+
 // Also ORs the types of all boundary links into *types (may be null).
 template <class L>
 __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsigned* types) {
@@ -1144,26 +1177,9 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsi
       atomicOr(types, TYPES_FLUID_LAST_LAYER);
     if (types != nullptr && ((!a.g.per[0] && x == 0) || (!a.g.per[1] && y == 0) || (!a.g.per[2] && z == 0)))
       atomicOr(types, TYPES_FLUID_FIRST_LAYER);
-    uint32_t m = 0;
-    for (int q = 1; q < L::Q; ++q) {
-      int sx = x - L::cx(q), sy = y - L::cy(q), sz = z - L::cz(q);
-      bool solid = false;
-      if (sx < 0 || sx >= a.g.nx) { if (!a.g.per[0]) solid = true; else sx = (sx + a.g.nx) % a.g.nx; }
-      if (sy < 0 || sy >= a.g.ny) { if (!a.g.per[1]) solid = true; else sy = (sy + a.g.ny) % a.g.ny; }
-      if (sz < 0 || sz >= a.g.nz) { if (!a.g.per[2]) solid = true; else sz = (sz + a.g.nz) % a.g.nz; }
-      int type = L_NOSLIP;
-      if (!solid && a.flags != nullptr) {
-        const uint8_t f = a.flags[sx + a.g.nx * (sy + a.g.ny * sz)];
-        solid = f != 0;
-        if (solid) type = link_type_of_flag(f);
-      }
-      if (solid) {
-        m |= 1u << q;
-        if (type != L_NOSLIP) m |= MASK_SPECIAL;
-        if (types != nullptr && type != L_NOSLIP) atomicOr(types, unsigned(type));
-      }
-    }
-    mask[cell] = m;
+    unsigned t = 0;
+    mask[cell] = cell_links<L>(a.g, a.flags, x, y, z, t);
+    if (types != nullptr && t != 0) atomicOr(types, t);
   }
 }
 

@@ -7,16 +7,21 @@
 // framework that reserves the GPU's memory at start-up and forbids further
 // cudaMalloc), or a time-step loop that cannot afford cudaMalloc's implicit
 // device-wide synchronisation.  This entry point takes the population array
-// and flags as they are, derives each cell's boundary links on the fly, and
+// and flags as they are, derives each cell's boundary links on the fly (with
+// the link-mask builder's own per-cell rule, cell_links), and
 // keeps its partial sums in a fixed array in the library's own device memory,
 // so it allocates nothing.
 //
-// The scratch is g_partials below: kMaxBlocks rows of 5 doubles (160 KiB),
-// held by every GPU that loads the library until the process exits.  Each
+// The scratch is g_partials below: kMaxBlocks rows of 5 doubles (160 KiB).
+// The runtime places it on a device when this module is loaded there; with
+// lazy module loading (the default of current toolkits) that happens at the
+// first call on the device, which can therefore itself take device memory,
+// and it stays until the process exits.  Each
 // block sums one chunk of kChunk cells, so at most kMaxBlocks * kChunk cells
 // (67,108,864) are accepted.  Every call shares the array: a call writes every
 // row it later reads, so nothing needs clearing, but two calls that overlap on
-// the GPU (for example on two streams) race on it.
+// the GPU (for example on two streams) race on it.  The call never
+// synchronises, so a non-finite sum is left in out for the caller to test.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -40,23 +45,6 @@ static __device__ __align__(256) double g_partials[kMaxBlocks * 5];
 std::mutex g_lock;
 double* g_addr[kMaxDevices] = {};
 
-// Boundary bits of one fluid cell from the flags (bit q: the source x - c_q
-// is not fluid), as in the link mask that a context would hold.
-template <class L>
-__device__ uint32_t links_from_flags(const Geom& g, const uint8_t* flags, int x, int y, int z) {
-  uint32_t m = 0;
-  for (int q = 1; q < L::Q; ++q) {
-    int sx = x - L::cx(q), sy = y - L::cy(q), sz = z - L::cz(q);
-    bool solid = false;
-    if (sx < 0 || sx >= g.nx) { if (!g.per[0]) solid = true; else sx = (sx + g.nx) % g.nx; }
-    if (sy < 0 || sy >= g.ny) { if (!g.per[1]) solid = true; else sy = (sy + g.ny) % g.ny; }
-    if (sz < 0 || sz >= g.nz) { if (!g.per[2]) solid = true; else sz = (sz + g.nz) % g.nz; }
-    if (!solid && flags != nullptr) solid = flags[sx + g.nx * (sy + g.ny * sz)] != 0;
-    if (solid) m |= 1u << q;
-  }
-  return m;
-}
-
 template <class L, class ST>
 __global__ void __launch_bounds__(kThreads) k_partial(const SweepArgs a, int view, double* partials) {
   const long long N = a.g.N;
@@ -67,7 +55,8 @@ __global__ void __launch_bounds__(kThreads) k_partial(const SweepArgs a, int vie
     if (a.flags != nullptr && a.flags[cell] != 0) continue;
     int x, y, z;
     cell_coords(a.g, cell, x, y, z);
-    const uint32_t mask = links_from_flags<L>(a.g, a.flags, x, y, z);
+    unsigned types = 0;
+    const uint32_t mask = cell_links<L>(a.g, a.flags, x, y, z, types);
     double f[L::Q];
     gather_f64<L, ST>(a, view, x, y, z, (int)cell, mask, f);
     double rho, rho0, u[3];

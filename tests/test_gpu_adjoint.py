@@ -6,7 +6,8 @@ Per-kernel parity (FP64 storage, 1e-12 relative): one adjoint step
 UBB links and a Guo force), the kinetic-energy seed, the equilibrium VJP.
 Whole-run parity: L, dL/du_0 and dL/dF of the checkpointed reverse sweep
 against the oracle's full reverse sweep (FP64: 1e-10; FP32 storage and
-adjoint: 1e-4).  Finite differences: directional derivatives of the FP64
+adjoint: 1e-4; FP16-shifted storage: 5e-3).  FP16-shifted single steps: the
+oracle linearised around the same binary16 state, 1e-5.  Finite differences: directional derivatives of the FP64
 forward on random directions (relative 1e-6 for the FP64 adjoint)."""
 import ctypes
 
@@ -86,6 +87,38 @@ def test_adjoint_step_parity(stencil, collision):
     assert _rel(dF.cpu().numpy()[: lat.d], ref_gF) < 1e-12
 
 
+@pytest.mark.parametrize("stencil,collision", [("D2Q9", "srt"), ("D3Q19", "trt"), ("D3Q19", "mrt"), ("D3Q27", "trt")])
+def test_f16s_adjoint_step_parity(stencil, collision):
+    """FP16-shifted storage: the adjoint step reads P_prev from binary16
+    storage and computes in FP32 with FP32 lambda.  The oracle linearises
+    around the same stored state (the binary16 values converted exactly to
+    FP64), so only the FP32 arithmetic differs: 1e-5 relative, the FP32
+    tolerance."""
+    shape = _shape(stencil)
+    fl = _flags(shape)
+    lat = olat.get(stencil)
+    sim = _gpu(stencil, collision, "f16s", shape, fl)
+    ref = _oracle(stencil, collision, shape, fl)
+    P = inputs.random_pdfs(lat.w, shape[::-1], seed=16)
+    lam = np.random.default_rng(3).standard_normal((lat.q,) + shape[::-1])
+    lam[:, fl != 0] = 0.0
+    sim.set_state(P.reshape(lat.q, -1))
+    raw, _ = sim.get_pdfs()
+    h16 = raw.view(torch.float16).reshape(lat.q, sim.N).double().cpu().numpy()
+    P16 = (h16 + lat.w[:, None]).reshape(P.shape)
+    lam_in = torch.tensor(lam.reshape(lat.q, -1), dtype=torch.float32, device=sim.device)
+    lam_out = torch.full_like(lam_in, float("nan"))
+    dF = torch.zeros(3, dtype=torch.float64, device=sim.device)
+    st = _lib.lib().lbm_adjoint_step(sim.ctx, raw.data_ptr(), lam_in.data_ptr(), lam_out.data_ptr(), dF.data_ptr())
+    assert st == 0
+    ref_lam, ref_gF = oad.adjoint_step(ref, P16, lam.astype(np.float32).astype(np.float64))
+    fluid = fl.reshape(-1) == 0
+    got = lam_out.cpu().numpy()
+    assert np.all(got[:, ~fluid] == 0.0)
+    assert _rel(got[:, fluid], ref_lam.reshape(lat.q, -1)[:, fluid]) < 1e-5
+    assert _rel(dF.cpu().numpy()[: lat.d], ref_gF) < 1e-5
+
+
 @pytest.mark.parametrize("stencil,collision", COMBOS)
 def test_seed_and_eq_vjp_parity(stencil, collision):
     shape = _shape(stencil)
@@ -121,8 +154,11 @@ def test_seed_and_eq_vjp_parity(stencil, collision):
 
 
 @pytest.mark.parametrize("stencil,collision", [("D2Q9", "srt"), ("D3Q19", "trt"), ("D3Q19", "mrt"), ("D3Q27", "trt")])
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4), ("f16s", 5e-3)])
 def test_whole_run_gradient_parity(stencil, collision, storage, tol):
+    """FP16-shifted storage differentiates its own binary16 trajectory, which
+    leaves the FP64 one by about the storage rounding per step; it is held to
+    the FP16 field tolerance, 5e-3."""
     shape = _shape(stencil)
     fl = _flags(shape)
     lat = olat.get(stencil)

@@ -166,8 +166,8 @@ lbm_status lbm_stencil_info(int32_t stencil, int32_t* q, int32_t* d, int32_t* c,
 /* Bytes the caller must allocate (the array layout that Sec. IV-D passes as
  * shape and stride, q values per cell as counted in Sec. V): pdf_bytes for
  * each population array (q * N * sizeof(storage)); aux_bytes for the auxiliary device buffer
- * (link mask and fluid-cell list of 4*N bytes each, used when flags or
- * non-periodic axes are present but reserved in every case, the list
+ * (link mask of 4*N bytes and fluid-cell list of 8*N bytes, used when flags
+ * or non-periodic axes are present but reserved in every case, the list
  * builder's counts and the reduction scratch).  Validates p. */
 lbm_status lbm_query_sizes(const lbm_params* p, size_t* pdf_bytes, size_t* aux_bytes);
 

@@ -66,7 +66,7 @@ struct lbm_ctx {
   double* partials = nullptr;
   double* result = nullptr;
   bool has_mask = false;
-  int* list = nullptr;  // fluid cells of a masked domain (SweepArgs::list)
+  uint2* list = nullptr;  // fluid cells of a masked domain with their mask words (SweepArgs::list)
   int n_main = 0, n_wrap = 0;
   unsigned link_types = 0;  // OR of the boundary-link types present (L_INLET, L_OUTLET)
   cudaStream_t stream = nullptr;
@@ -114,7 +114,7 @@ bool needs_mask(const lbm_params& p, bool has_flags) {
   return false;
 }
 
-// aux = [link mask: 4 N bytes][fluid-cell list: 4 N bytes][list-builder
+// aux = [link mask: 4 N bytes][fluid-cell list: 8 N bytes][list-builder
 // counts: 2 x 4 x nblk bytes][reduction partials][reduction result]; the mask
 // and list regions are always reserved so that the size does not depend on
 // the flags.
@@ -125,7 +125,7 @@ Layout layout_for(const lbm_params& p, long long N) {
   l.mask_off = 0;
   l.mask_bytes = align256(size_t(N) * 4);
   l.list_off = l.mask_bytes;
-  l.count_off = l.list_off + align256(size_t(N) * 4);
+  l.count_off = l.list_off + align256(size_t(N) * 8);
   l.part_off = l.count_off + align256(size_t(l.nblk) * 2 * sizeof(int));
   l.res_off = l.part_off + align256(size_t(kRedMaxBlocks) * 5 * sizeof(double));
   l.total = l.res_off + 256;
@@ -575,7 +575,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
       delete c;
       return LBM_E_UNSUPPORTED;
     }
-    c->list = reinterpret_cast<int*>(static_cast<char*>(aux) + lay.list_off);
+    c->list = reinterpret_cast<uint2*>(static_cast<char*>(aux) + lay.list_off);
     const lbm_status ls = build_list(c, a, lay);
     if (ls != LBM_OK) {
       delete c;

@@ -78,9 +78,11 @@ struct SweepArgs {
   // x wrap), as the AA even sweep does.
   const char* srci[27];
   char* dsti[27];
-  // masked domains: fluid cells in ascending order, n_main without wrapped
-  // neighbour accesses followed by n_wrap with
-  const int* list;
+  // masked domains: fluid cells in ascending order as (cell index, link-mask
+  // word) pairs, n_main without wrapped neighbour accesses followed by n_wrap
+  // with; the mask word is zero when a separate boundary kernel resolves the
+  // boundary links
+  const uint2* list;
   int n_main, n_wrap;
   int boundary_mode;  // LBM_BOUNDARY_SEPARATE: the sweep streams every link as fluid
   // masked sweeps: element offsets, relative to the cell and to the stream of
@@ -432,22 +434,22 @@ __device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& 
 // ------------------------------------------------------- fluid-cell lists
 // Domains with a link mask (flags or a non-periodic axis) are swept over the
 // list of their fluid cells in ascending order, so no warp carries lanes of
-// solid cells (in a porous channel most warps would).  The list holds the
-// plain cells first (n_main of them: no neighbour access wraps around a
-// periodic axis, no inlet or outlet link) and then the others (n_wrap),
-// which a second launch sweeps with coordinate-based addressing and the
-// inlet/outlet fix-ups, so the main launch has neither.  A no-slip link only
-// changes which slot is read (pull, AA odd) or written (AA odd, esoteric
-// twist), so the address is selected without branching.
+// solid cells (in a porous channel most warps would).  Each entry packs the
+// cell index with its link-mask word, so a thread reaches its populations
+// after one coalesced 8-byte load.  The list holds the cells without a
+// wrapped neighbour access first (n_main of them) and then the cells on a
+// face of a periodic axis (n_wrap), which a second launch sweeps with
+// coordinate-based addressing.  A no-slip link only changes which slot is
+// read (pull, AA odd) or written (AA odd, esoteric twist), so the address is
+// selected without branching; the few cells with an inlet or outlet link
+// (LBM_MASK_SPECIAL) take an out-of-line fix-up of those links' values.
 
-// 0: not fluid; 1: plain (no wrapped neighbour access, no inlet or outlet
-// link); 2: on a face of a periodic axis or with an inlet or outlet link
-// (the latter only for sweeps that resolve boundary links themselves)
+// 0: not fluid; 1: no wrapped neighbour access; 2: on a face of a periodic
+// axis
 template <class L>
 __device__ __forceinline__ int list_category(const SweepArgs& a, long long cell) {
   const uint32_t m = a.mask[cell];
   if (m & MASK_SOLID) return 0;
-  if ((m & MASK_SPECIAL) && !a.boundary_mode) return 2;
   int x, y, z;
   cell_coords(a.g, cell, x, y, z);
   bool wrap = (a.g.per[0] && (x == 0 || x == a.g.nx - 1)) || (a.g.per[1] && (y == 0 || y == a.g.ny - 1));
@@ -489,10 +491,11 @@ __global__ void __launch_bounds__(kListThreads) k_list_count(const SweepArgs a, 
 }
 
 // Writes each chunk's cells at its exclusive offsets (offsets[b] for main
-// cells, offsets[nblk + b] for wrap cells, both absolute), in ascending order.
+// cells, offsets[nblk + b] for wrap cells, both absolute), in ascending order,
+// each as (cell, link-mask word; zero with a separate boundary kernel).
 template <class L>
 __global__ void __launch_bounds__(kListThreads) k_list_scatter(const SweepArgs a, int nblk,
-                                                                const int* __restrict__ offsets, int* __restrict__ list) {
+                                                                const int* __restrict__ offsets, uint2* __restrict__ list) {
   __shared__ int warp_tot[2][kListThreads / 32];
   int base1 = offsets[blockIdx.x], base2 = offsets[nblk + blockIdx.x];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -512,18 +515,67 @@ __global__ void __launch_bounds__(kListThreads) k_list_scatter(const SweepArgs a
       tot1 += warp_tot[0][w];
       tot2 += warp_tot[1][w];
     }
-    if (cat == 1) list[base1 + pre1 + __popc(m1 & below)] = (int)cell;
-    if (cat == 2) list[base2 + pre2 + __popc(m2 & below)] = (int)cell;
+    const unsigned word = (cat != 0 && !a.boundary_mode) ? a.mask[cell] : 0u;
+    if (cat == 1) list[base1 + pre1 + __popc(m1 & below)] = make_uint2(unsigned(cell), word);
+    if (cat == 2) list[base2 + pre2 + __popc(m2 & below)] = make_uint2(unsigned(cell), word);
     base1 += tot1;
     base2 += tot2;
     __syncthreads();
   }
 }
 
+// Entry i of the list, loaded again after the collision: an asm with side
+// effects is neither hoisted above the collision nor merged with the first
+// load, so neither the entry nor its address stays in registers across it.
+__device__ __forceinline__ uint2 reload_entry(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
+// Inlet and outlet links of a pull sweep (cells with LBM_MASK_SPECIAL): v
+// holds the loaded populations, with P_qbar(x) on every boundary link; an
+// INLET link adds the UBB term, an OUTLET link takes f^eq_q(rho_out, u_P(x)).
+// Out of line and with scalar arguments, so the common path keeps neither
+// its registers nor the address of the kernel's parameter block.
+template <class L, class ST, bool DH>
+__device__ __noinline__ void pull_fixup(typename ST::T* v, const typename ST::S* src, long long N, int cell,
+                                        uint32_t mask, const uint8_t* flags, int nx, int ny, int nz, int perbits,
+                                        const OutletP op, double uw0, double uw1, double uw2) {
+  const int x = cell % nx, r = cell / nx, y = r % ny, z = r / ny;
+  for (int q = 1; q < L::Q; ++q) {
+    if (!((mask >> q) & 1u)) continue;
+    const int t = link_type(flags, nx, ny, nz, perbits, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+    const double ubb = 6.0 * L::w(q) * (L::cx(q) * uw0 + L::cy(q) * uw1 + L::cz(q) * uw2);
+    v[q] = pull_special<L, ST, DH>(src, N, cell, q, t, v[q], op, ubb);
+  }
+}
+
+// Inlet and outlet links of the single-array sweeps, after the collision: for
+// a boundary link (x, p = qbar) the value written for direction q is
+// B_p(P(x)) instead of P_q(x) (no-slip links need nothing: B_p = P_q).
+template <class L, class T, bool DH>
+__device__ __noinline__ void post_fixup(T* v, int cell, uint32_t mask, const uint8_t* flags, int nx, int ny, int nz,
+                                        int perbits, const OutletP op, double uw0, double uw1, double uw2) {
+  const int x = cell % nx, r = cell / nx, y = r % ny, z = r / ny;
+  T up[3];
+  {
+    T vv[L::Q];
+    for (int q = 0; q < L::Q; ++q) vv[q] = v[q];
+    post_velocity<L, T, DH>(vv, op, up);
+  }
+  for (int q = 1; q < L::Q; ++q) {
+    const int p = opp(q);
+    if (!((mask >> p) & 1u)) continue;
+    const int t = link_type(flags, nx, ny, nz, perbits, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+    if (t == L_INLET) v[q] += T(6.0 * L::w(p) * (L::cx(p) * uw0 + L::cy(p) * uw1 + L::cz(p) * uw2));
+    else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
+  }
+}
+
 // Sweep over list[0, n_main) (WRAP = false: every neighbour access is the
 // cell's own index plus a fixed offset) or over list[n_main, n_main + n_wrap)
-// (WRAP = true: neighbour indices from the coordinates, with wrapping, and the
-// inlet/outlet fix-ups).
+// (WRAP = true: neighbour indices from the coordinates, with wrapping).
 template <class L, class ST, int OP, int KIND, bool WRAP>
 __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
   using T = typename ST::T;
@@ -533,9 +585,9 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
   constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (WRAP ? a.n_wrap : a.n_main)) return;
-  const int cell = a.list[WRAP ? a.n_main + i : i];
-  // with a separate boundary kernel every link streams as a fluid link
-  const uint32_t mask = a.boundary_mode ? 0u : a.mask[cell];
+  const uint2 entry = a.list[WRAP ? a.n_main + i : i];
+  const int cell = int(entry.x);
+  const uint32_t mask = entry.y;
   T v[L::Q];
   if constexpr (WRAP) {
     int x, y, z;
@@ -581,43 +633,18 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
       }
     }
   }
-  if constexpr (KIND == K_PULL && WRAP) {
-    if (mask & MASK_SPECIAL) {
-      int x, y, z;
-      cell_coords(a.g, cell, x, y, z);
-      const OutletP op = outlet_params(a.cp);
-      for (int q = 1; q < L::Q; ++q) {
-        if ((mask >> q) & 1u) {
-          const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
-          const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
-                                              L::cz(q) * a.cp.u_wall[2]);
-          v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb);
-        }
-      }
-    }
+  if constexpr (KIND == K_PULL) {
+    if (mask & MASK_SPECIAL)
+      pull_fixup<L, ST, DH>(v, static_cast<const S*>(a.src), a.g.N, cell, mask, a.flags, a.g.nx, a.g.ny, a.g.nz,
+                            per_bits(a.g), outlet_params(a.cp), a.cp.u_wall[0], a.cp.u_wall[1], a.cp.u_wall[2]);
   }
 
   collide<L, T, DH>(v, a.cp, std::integral_constant<int, OP>{});
 
-  if constexpr (KIND != K_PULL && WRAP) {
-    // inlet/outlet links (x, p = qbar): the value written for direction q is
-    // B_p(P(x)) instead of P_q(x); no-slip links keep P_q(x) = B_p(P(x))
-    if (mask & MASK_SPECIAL) {
-      int x, y, z;
-      cell_coords(a.g, cell, x, y, z);
-      const OutletP op = outlet_params(a.cp);
-      T up[3];
-      post_velocity<L, T, DH>(v, op, up);
-#pragma unroll
-      for (int q = 1; q < L::Q; ++q) {
-        const int p = opp(q);
-        if ((mask >> p) & 1u) {
-          const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
-          if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
-          else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
-        }
-      }
-    }
+  if constexpr (KIND != K_PULL) {
+    if (mask & MASK_SPECIAL)
+      post_fixup<L, T, DH>(v, cell, mask, a.flags, a.g.nx, a.g.ny, a.g.nz, per_bits(a.g), outlet_params(a.cp),
+                           a.cp.u_wall[0], a.cp.u_wall[1], a.cp.u_wall[2]);
   }
   if constexpr (KIND == K_PULL) {
 #pragma unroll
@@ -647,12 +674,13 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
       pdf_st<S>(a, a.dstq[qd], idx, D::store(v[q], L::w(q)));
     }
   } else {
-    // cell and mask are read again (cache hits) rather than held across the
-    // collision: an asm with side effects is not hoisted above it
+    // the entry is read again (a cache hit) rather than held across the
+    // collision
     int tx;
     asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
-    const int cs = a.list[blockIdx.x * blockDim.x + tx];
-    const uint32_t ms = a.boundary_mode ? 0u : a.mask[cs];
+    const uint2 es = reload_entry(a.list + blockIdx.x * blockDim.x + tx);
+    const int cs = int(es.x);
+    const uint32_t ms = es.y;
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) {
       // AA odd: fluid A[q][x + c_q], boundary link (x, qbar) A[qbar][x];
@@ -709,8 +737,8 @@ __global__ void __launch_bounds__(kBlockX) k_boundary_pull(const SweepArgs a, ty
   using S = typename ST::S;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_main + a.n_wrap) return;
-  const int cell = a.list[i];
-  const uint32_t mask = a.mask[cell];
+  const int cell = int(a.list[i].x);
+  const uint32_t mask = a.mask[cell];  // the list's mask words are zero in this mode
   if ((mask & ((1u << L::Q) - 2u)) == 0) return;
   int x, y, z;
   cell_coords(a.g, cell, x, y, z);

@@ -104,7 +104,7 @@ cudaError_t launch_list_count(const SweepArgs& a, int nblk, int* counts, cudaStr
 }
 
 template <class L>
-cudaError_t launch_list_scatter(const SweepArgs& a, int nblk, const int* offsets, int* list, cudaStream_t s) {
+cudaError_t launch_list_scatter(const SweepArgs& a, int nblk, const int* offsets, uint2* list, cudaStream_t s) {
   k_list_scatter<L><<<nblk, kListThreads, 0, s>>>(a, nblk, offsets, list);
   return cudaGetLastError();
 }
@@ -122,7 +122,7 @@ struct OpsTable {
   cudaError_t (*ke_seed)(bool, const SweepArgs&, const int*, double*, void*, double*, cudaStream_t);
   cudaError_t (*eq_vjp)(const SweepArgs&, const double*, const double*, const void*, double*, cudaStream_t);
   cudaError_t (*list_count)(const SweepArgs&, int, int*, cudaStream_t);
-  cudaError_t (*list_scatter)(const SweepArgs&, int, const int*, int*, cudaStream_t);
+  cudaError_t (*list_scatter)(const SweepArgs&, int, const int*, uint2*, cudaStream_t);
   cudaError_t (*boundary_pull)(const SweepArgs&, void*, cudaStream_t);
 };
 

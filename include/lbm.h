@@ -275,6 +275,23 @@ lbm_status lbm_step_pull(lbm_ctx* ctx, const void* src, void* dst);
 lbm_status lbm_adjoint_step(lbm_ctx* ctx, const void* P_prev, const void* lam_in, void* lam_out,
                             double* dLdF);
 
+/* Reverse sweep of one checkpoint segment of n >= 1 steps, enqueued from the
+ * library so that no per-step host round trip is needed (not in the paper:
+ * the schedule of the sqrt(T) checkpointing the adjoint uses).
+ *   states: host array of n distinct device population arrays (pdf_bytes
+ *     each, storage type); states[0] holds the checkpoint P_s, states[1 ..
+ *     n-1] receive the recomputed P_{s+1} .. P_{s+n-1} (one lbm_step_pull
+ *     each);
+ *   lam0, lam1: the two adjoint arrays of lbm_adjoint_step (distinct, and
+ *     distinct from every state); *cur (0 or 1) names the one holding
+ *     lambda_{s+n} on entry and, on return, the one holding lambda_s;
+ *   dLdF: as in lbm_adjoint_step (accumulated over the n steps) or NULL.
+ * Then for t = s + n down to s + 1: lambda_{t-1} = adjoint_step(P_{t-1},
+ * lambda_t).  Same requirements and errors as lbm_step_pull and
+ * lbm_adjoint_step; LBM_E_INVAL for aliased buffers. */
+lbm_status lbm_adjoint_segment(lbm_ctx* ctx, void* const* states, int32_t n, void* lam0, void* lam1, int32_t* cur,
+                               double* dLdF);
+
 /* Not in the paper (the objective of the adjoint): kinetic energy in a box,
  * L = (1/2) sum rho |u|^2 over the fluid cells with
  * box[0] <= x < box[1], box[2] <= y < box[3], box[4] <= z < box[5], of the

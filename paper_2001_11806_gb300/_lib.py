@@ -59,6 +59,8 @@ _SIGS = {
     "lbm_set_force": (c_int32, [c_void_p, POINTER(c_double)]),
     "lbm_step_pull": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "lbm_adjoint_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_adjoint_segment": (c_int32, [c_void_p, POINTER(c_void_p), c_int32, c_void_p, c_void_p, POINTER(c_int32),
+                                      c_void_p]),
     "lbm_ke_loss_seed": (c_int32, [c_void_p, c_void_p, POINTER(c_int32), c_void_p, c_void_p, c_void_p]),
     "lbm_eq_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_reduce_noalloc": (c_int32, [POINTER(Params), c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),

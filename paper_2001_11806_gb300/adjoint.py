@@ -10,7 +10,9 @@ lambda_t) and finally dL/du_0 = (d f^eq / d u_0)^T lambda_0.
 Checkpointing (sqrt(T) scheme): the forward keeps the raw state every
 k = ceil(sqrt(T)) steps; the reverse sweep recomputes one segment of at most k
 states at a time from its checkpoint (one pull step per state, written
-straight into the segment buffers) and runs the adjoint backwards through it.
+straight into the segment buffers) and runs the adjoint backwards through it,
+one lbm_adjoint_segment call per segment, so the host issues one call per k
+steps.
 Device memory: (ceil(T/k) + k) population arrays plus two adjoint arrays; for
 D3Q19 FP32 at 128^3 and T = 1000 that is 64 x 159 MB = 10.2 GB.
 
@@ -88,19 +90,17 @@ class Rollout:
         self._loss(self._final, lam_out=lam[0], dLdF=dLdF)
         while len(self._seg) < self.k:
             self._seg.append(self._raw())
-        cur = 0
+        cur = ctypes.c_int32(0)
         nseg = math.ceil(self.T / self.k)
         for s in range(nseg - 1, -1, -1):
             base = s * self.k
-            end = min(base + self.k, self.T)
-            states = [self._ckpt[s]]
-            for i in range(1, end - base):
-                check(L.lbm_step_pull(ctx, states[-1].data_ptr(), self._seg[i].data_ptr()), ctx, "step_pull")
-                states.append(self._seg[i])
-            for t in range(end, base, -1):
-                check(L.lbm_adjoint_step(ctx, states[t - 1 - base].data_ptr(), lam[cur].data_ptr(),
-                                         lam[1 - cur].data_ptr(), dLdF.data_ptr()), ctx, "adjoint_step")
-                cur = 1 - cur
+            n = min(base + self.k, self.T) - base
+            # the library recomputes the segment into the buffers and runs its
+            # n adjoint steps backwards (lbm_adjoint_segment)
+            states = (ctypes.c_void_p * n)(self._ckpt[s].data_ptr(), *[self._seg[i].data_ptr() for i in range(1, n)])
+            check(L.lbm_adjoint_segment(ctx, states, n, lam[0].data_ptr(), lam[1].data_ptr(), ctypes.byref(cur),
+                                        dLdF.data_ptr()), ctx, "adjoint_segment")
+        cur = cur.value
         g_u0 = torch.empty((self.sim.d, N), dtype=torch.float64, device=self.device)
         check(L.lbm_eq_vjp(ctx, self._rho0.data_ptr(), self._u0.data_ptr(), lam[cur].data_ptr(), g_u0.data_ptr()),
               ctx, "eq_vjp")

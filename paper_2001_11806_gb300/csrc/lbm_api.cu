@@ -314,6 +314,7 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
   a.n_main = c->n_main;
   a.n_wrap = c->n_wrap;
   a.boundary_mode = c->p.boundary_mode;
+  a.special_wrap = (c->p.pattern == LBM_PULL && c->p.boundary_mode == LBM_BOUNDARY_IN_SWEEP) ? 1 : 0;
   a.pdf_bytes = c->pdf_bytes;
   a.bounds_flag = bounds_word(c);
   for (int q = 0; q < 27; ++q) {
@@ -774,6 +775,33 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const void* P_prev, const void* lam_in, 
   }
   cudaError_t e = c->ops.adjoint(c->p.collision, c->has_mask, a, lam_in, lam_out, dLdF, c->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "adjoint_step");
+}
+
+lbm_status lbm_adjoint_segment(lbm_ctx* c, void* const* states, int32_t n, void* lam0, void* lam1, int32_t* cur,
+                               double* dLdF) {
+  if (!c || !states || n < 1 || !lam0 || !lam1 || lam0 == lam1 || !cur || (*cur != 0 && *cur != 1))
+    return LBM_E_INVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!states[i] || states[i] == lam0 || states[i] == lam1) return LBM_E_INVAL;
+    for (int j = 0; j < i; ++j)
+      if (states[j] == states[i]) return LBM_E_INVAL;
+  }
+  lbm_status st = adjoint_ok(c);
+  if (st != LBM_OK) return st;
+  // recompute P_1 .. P_{n-1} of the segment, then run its adjoint backwards
+  for (int i = 1; i < n; ++i) {
+    st = lbm_step_pull(c, states[i - 1], states[i]);
+    if (st != LBM_OK) return st;
+  }
+  void* lam[2] = {lam0, lam1};
+  int k = *cur;
+  for (int t = n; t >= 1; --t) {
+    st = lbm_adjoint_step(c, states[t - 1], lam[k], lam[1 - k], dLdF);
+    if (st != LBM_OK) return st;
+    k = 1 - k;
+  }
+  *cur = k;
+  return LBM_OK;
 }
 
 lbm_status lbm_ke_loss_seed(lbm_ctx* c, const void* P, const int32_t box[6], double* L, void* lam_out,

@@ -85,6 +85,7 @@ struct SweepArgs {
   const uint2* list;
   int n_main, n_wrap;
   int boundary_mode;  // LBM_BOUNDARY_SEPARATE: the sweep streams every link as fluid
+  int special_wrap;   // list builder: cells with inlet/outlet links go to the second launch
   // masked sweeps: element offsets, relative to the cell and to the stream of
   // the lower slot of the pair (q, qbar), of the population direction q
   // reads (lf: fluid link, lb: boundary link) and writes (sf, sb: fluid or
@@ -445,11 +446,14 @@ __device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& 
 // (LBM_MASK_SPECIAL) take an out-of-line fix-up of those links' values.
 
 // 0: not fluid; 1: no wrapped neighbour access; 2: on a face of a periodic
-// axis
+// axis, or (two-grid pull resolving its boundary links in the sweep) with an
+// inlet or outlet link: the pull fixes those values up before the collision,
+// which the main launch does not carry
 template <class L>
 __device__ __forceinline__ int list_category(const SweepArgs& a, long long cell) {
   const uint32_t m = a.mask[cell];
   if (m & MASK_SOLID) return 0;
+  if ((m & MASK_SPECIAL) && a.special_wrap) return 2;
   int x, y, z;
   cell_coords(a.g, cell, x, y, z);
   bool wrap = (a.g.per[0] && (x == 0 || x == a.g.nx - 1)) || (a.g.per[1] && (y == 0 || y == a.g.ny - 1));
@@ -533,46 +537,6 @@ __device__ __forceinline__ uint2 reload_entry(const uint2* p) {
   return v;
 }
 
-// Inlet and outlet links of a pull sweep (cells with LBM_MASK_SPECIAL): v
-// holds the loaded populations, with P_qbar(x) on every boundary link; an
-// INLET link adds the UBB term, an OUTLET link takes f^eq_q(rho_out, u_P(x)).
-// Out of line and with scalar arguments, so the common path keeps neither
-// its registers nor the address of the kernel's parameter block.
-template <class L, class ST, bool DH>
-__device__ __noinline__ void pull_fixup(typename ST::T* v, const typename ST::S* src, long long N, int cell,
-                                        uint32_t mask, const uint8_t* flags, int nx, int ny, int nz, int perbits,
-                                        const OutletP op, double uw0, double uw1, double uw2) {
-  const int x = cell % nx, r = cell / nx, y = r % ny, z = r / ny;
-  for (int q = 1; q < L::Q; ++q) {
-    if (!((mask >> q) & 1u)) continue;
-    const int t = link_type(flags, nx, ny, nz, perbits, x - L::cx(q), y - L::cy(q), z - L::cz(q));
-    const double ubb = 6.0 * L::w(q) * (L::cx(q) * uw0 + L::cy(q) * uw1 + L::cz(q) * uw2);
-    v[q] = pull_special<L, ST, DH>(src, N, cell, q, t, v[q], op, ubb);
-  }
-}
-
-// Inlet and outlet links of the single-array sweeps, after the collision: for
-// a boundary link (x, p = qbar) the value written for direction q is
-// B_p(P(x)) instead of P_q(x) (no-slip links need nothing: B_p = P_q).
-template <class L, class T, bool DH>
-__device__ __noinline__ void post_fixup(T* v, int cell, uint32_t mask, const uint8_t* flags, int nx, int ny, int nz,
-                                        int perbits, const OutletP op, double uw0, double uw1, double uw2) {
-  const int x = cell % nx, r = cell / nx, y = r % ny, z = r / ny;
-  T up[3];
-  {
-    T vv[L::Q];
-    for (int q = 0; q < L::Q; ++q) vv[q] = v[q];
-    post_velocity<L, T, DH>(vv, op, up);
-  }
-  for (int q = 1; q < L::Q; ++q) {
-    const int p = opp(q);
-    if (!((mask >> p) & 1u)) continue;
-    const int t = link_type(flags, nx, ny, nz, perbits, x + L::cx(q), y + L::cy(q), z + L::cz(q));
-    if (t == L_INLET) v[q] += T(6.0 * L::w(p) * (L::cx(p) * uw0 + L::cy(p) * uw1 + L::cz(p) * uw2));
-    else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
-  }
-}
-
 // Sweep over list[0, n_main) (WRAP = false: every neighbour access is the
 // cell's own index plus a fixed offset) or over list[n_main, n_main + n_wrap)
 // (WRAP = true: neighbour indices from the coordinates, with wrapping).
@@ -633,18 +597,43 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
       }
     }
   }
-  if constexpr (KIND == K_PULL) {
-    if (mask & MASK_SPECIAL)
-      pull_fixup<L, ST, DH>(v, static_cast<const S*>(a.src), a.g.N, cell, mask, a.flags, a.g.nx, a.g.ny, a.g.nz,
-                            per_bits(a.g), outlet_params(a.cp), a.cp.u_wall[0], a.cp.u_wall[1], a.cp.u_wall[2]);
+  if constexpr (KIND == K_PULL && WRAP) {
+    if (mask & MASK_SPECIAL) {
+      int x, y, z;
+      cell_coords(a.g, cell, x, y, z);
+      const OutletP op = outlet_params(a.cp);
+      for (int q = 1; q < L::Q; ++q) {
+        if ((mask >> q) & 1u) {
+          const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
+          const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
+                                              L::cz(q) * a.cp.u_wall[2]);
+          v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb);
+        }
+      }
+    }
   }
 
   collide<L, T, DH>(v, a.cp, std::integral_constant<int, OP>{});
 
-  if constexpr (KIND != K_PULL) {
-    if (mask & MASK_SPECIAL)
-      post_fixup<L, T, DH>(v, cell, mask, a.flags, a.g.nx, a.g.ny, a.g.nz, per_bits(a.g), outlet_params(a.cp),
-                           a.cp.u_wall[0], a.cp.u_wall[1], a.cp.u_wall[2]);
+  if constexpr (KIND != K_PULL && WRAP) {
+    // inlet/outlet links (x, p = qbar): the value written for direction q is
+    // B_p(P(x)) instead of P_q(x); no-slip links keep P_q(x) = B_p(P(x))
+    if (mask & MASK_SPECIAL) {
+      int x, y, z;
+      cell_coords(a.g, cell, x, y, z);
+      const OutletP op = outlet_params(a.cp);
+      T up[3];
+      post_velocity<L, T, DH>(v, op, up);
+#pragma unroll
+      for (int q = 1; q < L::Q; ++q) {
+        const int p = opp(q);
+        if ((mask >> p) & 1u) {
+          const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+          if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
+          else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
+        }
+      }
+    }
   }
   if constexpr (KIND == K_PULL) {
 #pragma unroll
@@ -691,6 +680,40 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
       const int lo = q < p ? q : p;
       const unsigned idx = unsigned(cs) + (b ? a.sb[q] : a.sf[q]);
       pdf_st<S>(a, a.dstq[lo], idx, D::store(v[q], L::w(q)));
+    }
+  }
+  if constexpr (KIND != K_PULL && !WRAP) {
+    // Cells with inlet or outlet links (single-array patterns): every link
+    // was stored above as if it were a no-slip link (B_p(P(x)) = P_q(x) for
+    // p = qbar); the inlet and outlet ones are stored again with their own
+    // value B_p(P(x)) into the same slot.  After the stores, so that the
+    // common path carries none of this.
+    int tx;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+    const uint2 es = reload_entry(a.list + blockIdx.x * blockDim.x + tx);
+    if (es.y & MASK_SPECIAL) {
+      const int cs = int(es.x);
+      int x, y, z;
+      cell_coords(a.g, cs, x, y, z);
+      const OutletP op = outlet_params(a.cp);
+      T up[3];
+      post_velocity<L, T, DH>(v, op, up);
+#pragma unroll
+      for (int q = 1; q < L::Q; ++q) {
+        const int p = opp(q);
+        if ((es.y >> p) & 1u) {
+          const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+          if (t == L_INLET || t == L_OUTLET) {
+            const T val = t == L_INLET ? v[q] + ubb_term<L, T>(p, a.cp) : outlet_value<L, T, DH>(p, up, op);
+            if constexpr (KIND == K_AA_EVEN) {
+              pdf_st<S>(a, a.dstq[p], cs, D::store(val, L::w(q)));
+            } else {
+              const int lo = q < p ? q : p;
+              pdf_st<S>(a, a.dstq[lo], unsigned(cs) + a.sb[q], D::store(val, L::w(q)));
+            }
+          }
+        }
+      }
     }
   }
 }

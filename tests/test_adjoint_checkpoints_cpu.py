@@ -82,6 +82,19 @@ class FakeLib:
         _view(dLdF, 3)[:] += self.m.G.T @ lam
         return 0
 
+    def lbm_adjoint_segment(self, ctx, states, n, lam0, lam1, cur, dLdF):
+        """The documented schedule: recompute states[1 .. n-1], then n adjoint
+        steps backwards, alternating lam0/lam1 from *cur."""
+        for i in range(1, n):
+            self.lbm_step_pull(ctx, states[i - 1], states[i])
+        lam = [lam0, lam1]
+        k = cur._obj.value
+        for t in range(n, 0, -1):
+            self.lbm_adjoint_step(ctx, states[t - 1], lam[k], lam[1 - k], dLdF)
+            k = 1 - k
+        cur._obj.value = k
+        return 0
+
     def lbm_eq_vjp(self, ctx, rho0, u0, lam, g_u0):
         _view(g_u0, D * NC)[:] = self.m.E.T @ _view(lam, S)
         return 0

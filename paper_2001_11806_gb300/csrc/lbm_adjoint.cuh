@@ -148,6 +148,48 @@ __device__ __forceinline__ void collide_vjp(T drho, const T (&jh)[3], const T (&
   a_out = a;
 }
 
+// Body-force gradient of the adjoint sweep: every block writes the FP64 sum
+// of its cells' contributions to its own row of a scratch array (no
+// atomics: one address shared by all blocks of a 2 M-cell sweep serialised
+// tens of thousands of atomic adds per step), and k_force_rows_final adds the
+// rows in a fixed order to the caller's accumulator.
+template <class T>
+__device__ __forceinline__ void block_row3(const T (&v)[3], double* rows) {
+  __shared__ double sh[kBlockX / 32][3];
+  double s[3] = {double(v[0]), double(v[1]), double(v[2])};
+  for (int d = 0; d < 3; ++d) s[d] = warp_sum(s[d]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) sh[wid][d] = s[d];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x + 31) / 32; ++w) t += sh[w][threadIdx.x];
+    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    rows[b * 3 + threadIdx.x] = t;
+  }
+}
+
+// accum[0..2] += sum of rows[0 .. nrows) (one block of kForceThreads)
+constexpr int kForceThreads = 256;
+template <class R>
+__global__ void __launch_bounds__(kForceThreads) k_force_rows_final(const R* rows, long long nrows, R* accum) {
+  __shared__ R sh[kForceThreads / 32][3];
+  R s[3] = {0.0, 0.0, 0.0};
+  for (long long r = threadIdx.x; r < nrows; r += kForceThreads)
+    for (int d = 0; d < 3; ++d) s[d] += rows[r * 3 + d];
+  for (int d = 0; d < 3; ++d) s[d] = warp_sum(s[d]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) sh[wid][d] = s[d];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < kForceThreads / 32; ++w) t += sh[w][threadIdx.x];
+    accum[threadIdx.x] += t;
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void block_add3(T (&v)[3], double* accum) {
   // warp sums, then one FP64 atomic per warp and component
@@ -221,7 +263,7 @@ __device__ __forceinline__ double reload(const double* p) {
 // SweepArgs::dsti for lambda_out (base of stream q minus the offset of c_q).
 template <class L, class ST, int OP, bool BND>
 __global__ void __launch_bounds__(kBlockX) k_adjoint(const SweepArgs a, const typename ST::T* lam_in,
-                                                     typename ST::T* lam_out, double* dLdF) {
+                                                     typename ST::T* lam_out, double* force_rows) {
   using T = typename ST::T;
   using S = typename ST::S;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,7 +344,7 @@ __global__ void __launch_bounds__(kBlockX) k_adjoint(const SweepArgs a, const ty
       }
     }
   }
-  if (dLdF != nullptr && a.cp.has_force) block_add3(gF, dLdF);
+  if (force_rows != nullptr) block_row3(gF, force_rows);
 }
 
 // Kinetic energy in a box, L = (1/2) sum_{x in box, fluid} rho |u|^2 of the

@@ -64,6 +64,7 @@ struct lbm_ctx {
   const uint8_t* flags = nullptr;
   uint32_t* mask = nullptr;
   double* partials = nullptr;
+  double* force_rows = nullptr;  // per-block body-force sums of the adjoint sweep
   double* result = nullptr;
   bool has_mask = false;
   uint2* list = nullptr;  // fluid cells of a masked domain with their mask words (SweepArgs::list)
@@ -97,7 +98,7 @@ constexpr int kGraphSteps = 32;
 constexpr long long kGraphMaxCells = 1 << 20;
 
 struct Layout {
-  size_t mask_off, mask_bytes, list_off, count_off, part_off, res_off, total;
+  size_t mask_off, mask_bytes, list_off, count_off, part_off, adj_off, res_off, total;
   int nblk;  // chunks of the fluid-list builder
 };
 
@@ -115,11 +116,11 @@ bool needs_mask(const lbm_params& p, bool has_flags) {
 }
 
 // aux = [link mask: 4 N bytes][fluid-cell list: 8 N bytes][list-builder
-// counts: 2 x 4 x nblk bytes][reduction partials][reduction result]; the mask
+// counts: 2 x 4 x nblk bytes][reduction partials][adjoint force rows: 3
+// doubles per sweep block][reduction result]; the mask
 // and list regions are always reserved so that the size does not depend on
 // the flags.
 Layout layout_for(const lbm_params& p, long long N) {
-  (void)p;
   Layout l;
   l.nblk = int((N + kListChunk - 1) / kListChunk);
   l.mask_off = 0;
@@ -127,7 +128,12 @@ Layout layout_for(const lbm_params& p, long long N) {
   l.list_off = l.mask_bytes;
   l.count_off = l.list_off + align256(size_t(N) * 8);
   l.part_off = l.count_off + align256(size_t(l.nblk) * 2 * sizeof(int));
-  l.res_off = l.part_off + align256(size_t(kRedMaxBlocks) * 5 * sizeof(double));
+  Geom g{};
+  g.nx = p.nx;
+  g.ny = p.ny;
+  g.nz = p.nz;
+  l.adj_off = l.part_off + align256(size_t(kRedMaxBlocks) * 5 * sizeof(double));
+  l.res_off = l.adj_off + align256(size_t(adjoint_rows(g)) * 3 * sizeof(double));
   l.total = l.res_off + 256;
   return l;
 }
@@ -545,6 +551,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
   c->has_mask = mask;
   c->mask = mask ? reinterpret_cast<uint32_t*>(static_cast<char*>(aux) + lay.mask_off) : nullptr;
   c->partials = reinterpret_cast<double*>(static_cast<char*>(aux) + lay.part_off);
+  c->force_rows = reinterpret_cast<double*>(static_cast<char*>(aux) + lay.adj_off);
   c->result = reinterpret_cast<double*>(static_cast<char*>(aux) + lay.res_off);
   c->stream = static_cast<cudaStream_t>(stream);
   fill_collide_params(c);
@@ -773,7 +780,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, const void* P_prev, const void* lam_in, 
       a.dsti[q] = reinterpret_cast<char*>(reinterpret_cast<uintptr_t>(lam_out) + (q * c->N - off) * el);
     }
   }
-  cudaError_t e = c->ops.adjoint(c->p.collision, c->has_mask, a, lam_in, lam_out, dLdF, c->stream);
+  cudaError_t e = c->ops.adjoint(c->p.collision, c->has_mask, a, lam_in, lam_out, dLdF, c->force_rows, c->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "adjoint_step");
 }
 

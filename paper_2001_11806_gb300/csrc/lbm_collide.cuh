@@ -159,13 +159,16 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
   }
   T F[3] = {T(0), T(0), T(0)};
   const bool force = p.has_force != 0;
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  // u0: velocity without the Guo half force, for the odd equilibrium part
+  // (see the pair loop); u: with it (Eq. density)
+  const T u0[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
   if (force) {
     F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
     jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
   }
-  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
-  const T inv = T(1) / rho0;
-  const T u[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
+  const T u[3] = {force ? jx * inv : u0[0], force ? jy * inv : u0[1], L::D == 3 && force ? jz * inv : u0[2]};
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0;
@@ -213,14 +216,26 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
     const T w = T(L::w(q));
     const T cu = cdot<L, T>(q, u);
     T A = fma(c1, s[k], (oe * w) * fma(k45, cu * cu, base));
-    T B = fma(c2, d[k], (m3o * w) * cu);
     if (force) {
+      // The force's whole odd contribution is z = 3 w_q c_q.F (its half in
+      // h^eq- relaxed by omega_o plus (1 - omega_o/2) G- sum to it), so B
+      // takes h^eq- of the momentum without the half force.  z is the same
+      // constant in every cell: added to B, which lies on the coarse FP32
+      // grid of the populations, it would be rounded by the same amount in
+      // every cell of a binade and bias the injected momentum (1e-4 of F at
+      // F = 1e-6, |h| ~ 1e-3); added to the small even part A first, it is
+      // rounded on a fine grid and the final rounding of A + B is unbiased.
       const T cF = cdot<L, T>(q, F);
       A += ge * w * (T(9) * cu * cF - uF3);
-      B += go * w * T(3) * cF;
+      const T B = fma(c2, d[k], (m3o * w) * cdot<L, T>(q, u0));
+      const T z = T(3) * w * cF;
+      v[q] = DH ? (A + z) + B : w + ((A + z) + B);
+      v[q + 1] = DH ? (A - z) - B : w + ((A - z) - B);
+    } else {
+      const T B = fma(c2, d[k], (m3o * w) * cu);
+      v[q] = DH ? A + B : w + (A + B);
+      v[q + 1] = DH ? A - B : w + (A - B);
     }
-    v[q] = DH ? A + B : w + (A + B);
-    v[q + 1] = DH ? A - B : w + (A - B);
   }
 }
 
@@ -388,13 +403,15 @@ __device__ __forceinline__ void collide_mrt3(T (&h)[L::Q], const CollideParams& 
   }
   T F[3] = {T(0), T(0), T(0)};
   const bool force = p.has_force != 0;
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  // u0 without the Guo half force (odd parts), u with it (Eq. density)
+  const T u0[3] = {jx * inv, jy * inv, D == 3 ? jz * inv : T(0)};
   if (force) {
     F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
     jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
   }
-  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
-  const T inv = T(1) / rho0;
-  const T u[3] = {jx * inv, jy * inv, D == 3 ? jz * inv : T(0)};
+  const T u[3] = {force ? jx * inv : u0[0], force ? jy * inv : u0[1], D == 3 && force ? jz * inv : u0[2]};
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0, k3 = T(3) * rho0;
@@ -447,11 +464,23 @@ __device__ __forceinline__ void collide_mrt3(T (&h)[L::Q], const CollideParams& 
     // even part: s/2 + G+ - omega_h ys/2 - projections; odd part: d/2 + G- - omega_h yd/2
     const T hs = T(0.5) * (h[q] + h[q + 1]);
     const T hd = T(0.5) * (h[q] - h[q + 1]);
-    const T yd = dd[k] - T(2) * w * k3 * cu + Gd;
-    const T A = hs + Gs - T(0.5) * oh * s[k] - proj;
-    const T B = hd + Gd - T(0.5) * oh * yd;
-    h[q] = A + B;
-    h[q + 1] = A - B;
+    if (force) {
+      // yd from the momentum without the half force (the F/2 in h^eq- and
+      // G-/2 cancel), and the constant G- = 3 w c.F added to the small
+      // relaxation term before the coarse populations (unbiased rounding,
+      // see collide_pairs)
+      const T yd = dd[k] - T(2) * w * k3 * cdot<L, T>(q, u0);
+      const T X = Gs - T(0.5) * oh * s[k] - proj;
+      const T B = hd - T(0.5) * oh * yd;
+      h[q] = (hs + (X + Gd)) + B;
+      h[q + 1] = (hs + (X - Gd)) - B;
+    } else {
+      const T yd = dd[k] - T(2) * w * k3 * cu;
+      const T A = hs - T(0.5) * oh * s[k] - proj;
+      const T B = hd - T(0.5) * oh * yd;
+      h[q] = A + B;
+      h[q + 1] = A - B;
+    }
   }
 }
 
@@ -574,17 +603,26 @@ __device__ __forceinline__ void mrt_forward_pairs(T g0, const T (&gs)[(L::Q - 1)
   ((d[Ks] = mrt_delta_pairs<L, T, Ks>(g0, gs, gd, p)), ...);
 }
 
+// With a force, the Guo terms join the (small) relaxation term before the
+// populations are added, so that the constant G- = 3 w c.F is not rounded on
+// the coarse grid of h (see collide_pairs).
 template <class L, class T, int... Ps>
 __device__ __forceinline__ void mrt_backward_pairs(T (&h)[L::Q], const T (&d)[L::Q], const T (&Gs)[(L::Q - 1) / 2],
-                                                   const T (&Gd)[(L::Q - 1) / 2], std::integer_sequence<int, Ps...>) {
+                                                   const T (&Gd)[(L::Q - 1) / 2], bool force,
+                                                   std::integer_sequence<int, Ps...>) {
   constexpr auto ks = std::make_integer_sequence<int, L::Q>{};
   (([&] {
      constexpr int q = 2 * Ps + 1;
      const T E = mrt_col_par<L, T, 0, q>(d, ks);
      const T O = mrt_col_par<L, T, 1, q>(d, ks);
      const T w = T(L::w(q));
-     h[q] = h[q] + Gs[Ps] + Gd[Ps] - w * (E + O);
-     h[q + 1] = h[q + 1] + Gs[Ps] - Gd[Ps] - w * (E - O);
+     if (force) {
+       h[q] = h[q] + ((Gs[Ps] + Gd[Ps]) - w * (E + O));
+       h[q + 1] = h[q + 1] + ((Gs[Ps] - Gd[Ps]) - w * (E - O));
+     } else {
+       h[q] = h[q] - w * (E + O);
+       h[q + 1] = h[q + 1] - w * (E - O);
+     }
    }()),
    ...);
 }
@@ -608,13 +646,15 @@ __device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p
   }
   T F[3] = {T(0), T(0), T(0)};
   const bool force = p.has_force != 0;
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  // u0 without the Guo half force (odd parts), u with it (Eq. density)
+  const T u0[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
   if (force) {
     F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
     jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
   }
-  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
-  const T inv = T(1) / rho0;
-  const T u[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
+  const T u[3] = {force ? jx * inv : u0[0], force ? jy * inv : u0[1], L::D == 3 && force ? jz * inv : u0[2]};
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0, k3 = T(3) * rho0;
@@ -637,12 +677,14 @@ __device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p
       Gd[k] = w * T(3) * cF;
     }
     gs[k] = s[k] - T(2) * w * fma(k45, cu * cu, base) + Gs[k];
-    gd[k] = dd[k] - T(2) * w * k3 * cu + Gd[k];
+    // odd part: the F/2 of h^eq- and G-/2 cancel, so g- needs only the
+    // momentum without the half force
+    gd[k] = dd[k] - T(2) * w * k3 * cdot<L, T>(q, u0);
   }
   T d[L::Q];
   mrt_forward_pairs<L, T>(g0, gs, gd, d, p, std::make_integer_sequence<int, L::Q>{});
   h[0] = h[0] + G0 - T(L::w(0)) * mrt_col_par<L, T, 0, 0>(d, std::make_integer_sequence<int, L::Q>{});
-  mrt_backward_pairs<L, T>(h, d, Gs, Gd, std::make_integer_sequence<int, NP>{});
+  mrt_backward_pairs<L, T>(h, d, Gs, Gd, force, std::make_integer_sequence<int, NP>{});
 }
 
 }  // namespace lbm

@@ -1324,6 +1324,11 @@ inline dim3 sweep_grid(const Geom& g) {
   const dim3 b = sweep_block(g);
   return dim3((g.nx + b.x - 1) / b.x, g.ny, g.nz);
 }
+// blocks of a sweep_grid launch (rows of the adjoint's force scratch)
+inline long long adjoint_rows(const Geom& g) {
+  const dim3 gr = sweep_grid(g);
+  return (long long)gr.x * gr.y * gr.z;
+}
 
 template <class L, class ST, int OP, int KIND>
 cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {

@@ -50,20 +50,27 @@ struct Ops {
     return cudaGetLastError();
   }
   using T = typename ST::T;
+  // rows: scratch of adjoint_rows(g) x 3 doubles for the per-block force
+  // sums when dF is non-null (and the sweep has a force)
   template <int OP>
-  static cudaError_t adjoint_op(bool bnd, const SweepArgs& a, const void* li, void* lo, double* dF, cudaStream_t s) {
+  static cudaError_t adjoint_op(bool bnd, const SweepArgs& a, const void* li, void* lo, double* dF, double* rows,
+                                cudaStream_t s) {
+    double* r = (dF != nullptr && a.cp.has_force) ? rows : nullptr;
     if (bnd)
-      k_adjoint<L, ST, OP, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, (const T*)li, (T*)lo, dF);
+      k_adjoint<L, ST, OP, true><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, (const T*)li, (T*)lo, r);
     else
-      k_adjoint<L, ST, OP, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, (const T*)li, (T*)lo, dF);
+      k_adjoint<L, ST, OP, false><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a, (const T*)li, (T*)lo, r);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || r == nullptr) return e;
+    k_force_rows_final<double><<<1, kForceThreads, 0, s>>>(r, adjoint_rows(a.g), dF);
     return cudaGetLastError();
   }
   static cudaError_t adjoint(int op, bool bnd, const SweepArgs& a, const void* li, void* lo, double* dF,
-                             cudaStream_t s) {
+                             double* rows, cudaStream_t s) {
     switch (op) {
-      case OP_SRT: return adjoint_op<OP_SRT>(bnd, a, li, lo, dF, s);
-      case OP_TRT: return adjoint_op<OP_TRT>(bnd, a, li, lo, dF, s);
-      case OP_MRT: return adjoint_op<OP_MRT>(bnd, a, li, lo, dF, s);
+      case OP_SRT: return adjoint_op<OP_SRT>(bnd, a, li, lo, dF, rows, s);
+      case OP_TRT: return adjoint_op<OP_TRT>(bnd, a, li, lo, dF, rows, s);
+      case OP_MRT: return adjoint_op<OP_MRT>(bnd, a, li, lo, dF, rows, s);
     }
     return cudaErrorInvalidValue;
   }
@@ -118,7 +125,7 @@ struct OpsTable {
   cudaError_t (*reduce_partial)(int, const SweepArgs&, double*, int, cudaStream_t);
   cudaError_t (*set_state)(int, int, const SweepArgs&, const double*, const double*, const double*, cudaStream_t);
   cudaError_t (*link_mask)(const SweepArgs&, uint32_t*, unsigned*, cudaStream_t);
-  cudaError_t (*adjoint)(int, bool, const SweepArgs&, const void*, void*, double*, cudaStream_t);
+  cudaError_t (*adjoint)(int, bool, const SweepArgs&, const void*, void*, double*, double*, cudaStream_t);
   cudaError_t (*ke_seed)(bool, const SweepArgs&, const int*, double*, void*, double*, cudaStream_t);
   cudaError_t (*eq_vjp)(const SweepArgs&, const double*, const double*, const void*, double*, cudaStream_t);
   cudaError_t (*list_count)(const SweepArgs&, int, int*, cudaStream_t);

@@ -142,7 +142,7 @@ class ClockSampler:
 
     def _reader(self):
         for line in self.proc.stdout:
-            self.lines.append(line)
+            self.lines.append((time.time(), line))
 
     def start(self):
         import threading
@@ -160,6 +160,24 @@ class ClockSampler:
             time.sleep(0.05)
         self.skip = len(self.lines)
 
+    @staticmethod
+    def _text(entry):
+        return entry[1] if isinstance(entry, tuple) else entry
+
+    def window_mhz(self, t0, t1):
+        """Median SM clock of the samples that arrived between host times t0
+        and t1 (None when the window held no sample)."""
+        sm = []
+        for entry in self.lines:
+            if not isinstance(entry, tuple) or not (t0 <= entry[0] <= t1):
+                continue
+            parts = [p.strip() for p in entry[1].split(",")]
+            try:
+                sm.append(float(parts[1]))
+            except (IndexError, ValueError):
+                continue
+        return float(np.median(sm)) if sm else None
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -173,7 +191,8 @@ class ClockSampler:
             self.thread.join(timeout=5)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines[self.skip:]:
+        for entry in self.lines[self.skip:]:
+            line = self._text(entry)
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -192,17 +211,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample_run(steps, warmup, budget_s=None):
-    """The FP64 oracle on a REF_SIDE^3 periodic box of the same workload."""
+def oracle_sample_run(steps, warmup, budget_s=None, side=REF_SIDE, barrier=None):
+    """The FP64 oracle on a side^3 periodic box of the same workload: (MLUPS,
+    steps timed, seconds)."""
     from oracle import collision as oco
     from oracle import lattice as olat
     from oracle import lbm as olbm
     from paper_2001_11806_gb300 import inputs
     lat = olat.d3q19()
-    sim = olbm.Sim(oco.Method(lat, "trt", [OMEGA_E, oco.trt_odd_rate(OMEGA_E, MAGIC)]), (REF_SIDE,) * 3)
-    rho, u = inputs.tgv3d(REF_SIDE, U0, NOISE, SEED)
+    sim = olbm.Sim(oco.Method(lat, "trt", [OMEGA_E, oco.trt_odd_rate(OMEGA_E, MAGIC)]), (side,) * 3)
+    rho, u = inputs.tgv3d(side, U0, NOISE, SEED)
     sim.init_equilibrium(rho, u)
     sim.step(warmup)
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
     done = 0
     while done < steps:
@@ -211,25 +233,68 @@ def oracle_sample_run(steps, warmup, budget_s=None):
         if budget_s is not None and time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return REF_SIDE ** 3 * done / dt / 1e6, done, dt
+    return side ** 3 * done / dt / 1e6, done, dt
 
 
-REF_BUDGET_S = 150.0  # the reference arm stops timing after this many seconds
+def _oracle_worker(args):
+    steps, warmup, budget_s, side, barrier = args
+    return oracle_sample_run(steps, warmup, budget_s, side, barrier)
+
+
+def host_cpu():
+    """CPU model name and logical core count of this host (lscpu, else
+    /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return model, os.cpu_count() or 1
+
+
+def oracle_parallel_run(procs, steps, warmup, budget_s, side):
+    """The oracle timed on `procs` host cores at once: one spawned process
+    per core, each stepping its own side^3 box of the workload (the oracle
+    itself is unchanged and single-threaded; BLAS threads are pinned to 1).
+    Returns (aggregate MLUPS, steps of the slowest process, seconds)."""
+    import multiprocessing as mpl
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    if procs <= 1:
+        return oracle_sample_run(steps, warmup, budget_s, side)
+    ctx = mpl.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(procs)
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(steps, warmup, budget_s, side, barrier)] * procs)
+    cells_steps = sum(side ** 3 * done for _, done, _ in res)
+    wall = max(dt for _, _, dt in res)
+    return cells_steps / wall / 1e6, min(done for _, done, _ in res), wall
+
+
+REF_BUDGET_S = 120.0  # the reference arm stops timing after this many seconds
+CPU_SIDE = 64  # box edge of each oracle process
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    mlups, done, dt = oracle_sample_run(args.steps, args.warmup, budget_s=REF_BUDGET_S)
-    sample = f"FP64 numpy oracle, {REF_SIDE}^3 periodic box of the same TGV workload per step, {done} steps"
+    model, cores = host_cpu()
+    mlups, done, dt = oracle_parallel_run(cores, args.steps, args.warmup, REF_BUDGET_S, CPU_SIDE)
+    sample = (f"FP64 numpy oracle, one {CPU_SIDE}^3 periodic box of the same TGV workload per process on "
+              f"{cores} processes ({model}), {done} steps each")
     if done < args.steps:
         sample += f" (of {args.steps} requested; timing stops after {REF_BUDGET_S:.0f} s)"
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
             "ms_per_step": round(1e3 * dt / done, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{REF_SIDE}^3 box"},
-            "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD, "sample": f"{cores} x {CPU_SIDE}^3 boxes", "cpu_model": model},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -334,8 +399,21 @@ def run_variants(device, peak, only=None, steps_override=None, warmup=10):
         torch.cuda.empty_cache()
     if only is not None:
         return out
-    # adjoint step cost against the forward step (D3Q19 TRT FP32 128^3)
-    from paper_2001_11806_gb300 import _lib
+    out += run_adjoint(device, peak)
+    return out
+
+
+def run_adjoint(device, peak, T=1000):
+    """Config 5 (D3Q19 TRT FP32 128^3 TGV, uniform force 1e-6): one adjoint
+    step against one forward step, and the whole gradient (forward with
+    sqrt(T) checkpoints, seed, recomputation and reverse sweep) against T
+    forward steps."""
+    import torch
+
+    from paper_2001_11806_gb300 import _lib, inputs
+    from paper_2001_11806_gb300.adjoint import Rollout
+    from paper_2001_11806_gb300.sim import Sim
+    out = []
     sim = Sim("D3Q19", "trt", "f32", "pull", (128,) * 3, omega=[OMEGA_E], trt_magic=MAGIC, force=[1e-6, 0, 0],
               device=device)
     rho, u = inputs.tgv3d(128, U0, NOISE, SEED)
@@ -343,7 +421,9 @@ def run_variants(device, peak, only=None, steps_override=None, warmup=10):
     sim.step(10)
     fwd = _time_steps(sim, 200, torch)
     raw, _ = sim.get_pdfs()
-    lam = [torch.zeros((19, sim.N), dtype=torch.float32, device=device) for _ in range(2)]
+    # a dense adjoint field (every force row non-zero), as in a real reverse sweep
+    gen = torch.Generator(device=device).manual_seed(5)
+    lam = [torch.randn((19, sim.N), dtype=torch.float32, device=device, generator=gen) for _ in range(2)]
     dF = torch.zeros(3, dtype=torch.float64, device=device)
     stream = torch.cuda.current_stream(sim.device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -362,6 +442,32 @@ def run_variants(device, peak, only=None, steps_override=None, warmup=10):
                 "forward_ms_per_step": round(fwd, 4), "adjoint_over_forward": round(adj / fwd, 3),
                 "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
     sim.close()
+    del sim, lam, raw
+    torch.cuda.empty_cache()
+    box = (48, 80, 48, 80, 48, 80)
+    rho0, u0 = rho.reshape(-1), u.reshape(3, -1)
+    ro = Rollout("D3Q19", "trt", "f32", (128,) * 3, [OMEGA_E], T, box, trt_magic=MAGIC, device=device)
+    ro.gradient(rho0, u0, [1e-6, 0.0, 0.0])
+    stream = torch.cuda.current_stream(device)
+    reps = []
+    for _ in range(3):
+        e0.record(stream)
+        ro.gradient(rho0, u0, [1e-6, 0.0, 0.0])
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        grad_ms = e0.elapsed_time(e1)
+        e0.record(stream)
+        ro.loss(rho0, u0, [1e-6, 0.0, 0.0])
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        reps.append((grad_ms, e0.elapsed_time(e1)))
+    grad_ms, loss_ms = sorted(reps)[1]
+    out.append({"workload": f"D3Q19 TRT FP32 128^3 gradient of the box kinetic energy, T = {T}, sqrt(T) checkpoints",
+                "gradient_ms": round(grad_ms, 2), "forward_ms": round(loss_ms, 2),
+                "gradient_over_forward": round(grad_ms / loss_ms, 3),
+                "checkpoint_buffers": len(ro._ckpt) + len(ro._seg)})
+    del ro
+    torch.cuda.empty_cache()
     return out
 
 

@@ -159,16 +159,13 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
   }
   T F[3] = {T(0), T(0), T(0)};
   const bool force = p.has_force != 0;
-  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
-  const T inv = T(1) / rho0;
-  // u0: velocity without the Guo half force, for the odd equilibrium part
-  // (see the pair loop); u: with it (Eq. density)
-  const T u0[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
   if (force) {
     F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
     jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
   }
-  const T u[3] = {force ? jx * inv : u0[0], force ? jy * inv : u0[1], L::D == 3 && force ? jz * inv : u0[2]};
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0;
@@ -202,7 +199,7 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
     else if (p.smag_magic) oo = T(1) / (T(p.smag_lambda) / (tau - T(0.5)) + T(0.5));
   }
   const T c1 = T(0.5) - T(0.5) * oe, c2 = T(0.5) - T(0.5) * oo;
-  const T m3o = T(3) * rho0 * oo;
+  const T m3o = T(3) * rho0 * oo, m3 = T(3) * rho0;
   const T ge = T(1) - T(0.5) * oe, go = T(1) - T(0.5) * oo;
   const T uF3 = T(3) * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
   {
@@ -217,20 +214,20 @@ __device__ __forceinline__ void collide_pairs(T (&v)[L::Q], const CollideParams&
     const T cu = cdot<L, T>(q, u);
     T A = fma(c1, s[k], (oe * w) * fma(k45, cu * cu, base));
     if (force) {
-      // The force's whole odd contribution is z = 3 w_q c_q.F (its half in
-      // h^eq- relaxed by omega_o plus (1 - omega_o/2) G- sum to it), so B
-      // takes h^eq- of the momentum without the half force.  z is the same
-      // constant in every cell: added to B, which lies on the coarse FP32
-      // grid of the populations, it would be rounded by the same amount in
-      // every cell of a binade and bias the injected momentum (1e-4 of F at
-      // F = 1e-6, |h| ~ 1e-3); added to the small even part A first, it is
-      // rounded on a fine grid and the final rounding of A + B is unbiased.
+      // Odd part as d/2 + X with X = -omega_o (d/2 - h^eq-) + (1 - omega_o/2)
+      // G-: the Guo term G- = 3 w_q c_q.F is the same constant in every
+      // cell, and added to a value on the coarse FP32 grid of the
+      // populations it would be rounded by the same amount in every cell of
+      // a binade, biasing the injected momentum (1e-4 of F at F = 1e-6,
+      // |h| ~ 1e-3).  X is a small, varying non-equilibrium term, so the
+      // constant is rounded on a fine grid and the final rounding of
+      // d/2 + X is unbiased.
       const T cF = cdot<L, T>(q, F);
       A += ge * w * (T(9) * cu * cF - uF3);
-      const T B = fma(c2, d[k], (m3o * w) * cdot<L, T>(q, u0));
-      const T z = T(3) * w * cF;
-      v[q] = DH ? (A + z) + B : w + ((A + z) + B);
-      v[q + 1] = DH ? (A - z) - B : w + ((A - z) - B);
+      const T X = fma(go * w * T(3), cF, -oo * fma(T(0.5), d[k], -(m3 * w) * cu));
+      const T B = fma(T(0.5), d[k], X);
+      v[q] = DH ? A + B : w + (A + B);
+      v[q + 1] = DH ? A - B : w + (A - B);
     } else {
       const T B = fma(c2, d[k], (m3o * w) * cu);
       v[q] = DH ? A + B : w + (A + B);
@@ -403,15 +400,13 @@ __device__ __forceinline__ void collide_mrt3(T (&h)[L::Q], const CollideParams& 
   }
   T F[3] = {T(0), T(0), T(0)};
   const bool force = p.has_force != 0;
-  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
-  const T inv = T(1) / rho0;
-  // u0 without the Guo half force (odd parts), u with it (Eq. density)
-  const T u0[3] = {jx * inv, jy * inv, D == 3 ? jz * inv : T(0)};
   if (force) {
     F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
     jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
   }
-  const T u[3] = {force ? jx * inv : u0[0], force ? jy * inv : u0[1], D == 3 && force ? jz * inv : u0[2]};
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, D == 3 ? jz * inv : T(0)};
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0, k3 = T(3) * rho0;
@@ -465,11 +460,10 @@ __device__ __forceinline__ void collide_mrt3(T (&h)[L::Q], const CollideParams& 
     const T hs = T(0.5) * (h[q] + h[q + 1]);
     const T hd = T(0.5) * (h[q] - h[q + 1]);
     if (force) {
-      // yd from the momentum without the half force (the F/2 in h^eq- and
-      // G-/2 cancel), and the constant G- = 3 w c.F added to the small
-      // relaxation term before the coarse populations (unbiased rounding,
-      // see collide_pairs)
-      const T yd = dd[k] - T(2) * w * k3 * cdot<L, T>(q, u0);
+      // the constant G- = 3 w c.F joins the small, varying relaxation terms
+      // before the coarse populations are added (unbiased rounding, see
+      // collide_pairs); yd is small, so its own Gd is rounded finely
+      const T yd = dd[k] - T(2) * w * k3 * cu + Gd;
       const T X = Gs - T(0.5) * oh * s[k] - proj;
       const T B = hd - T(0.5) * oh * yd;
       h[q] = (hs + (X + Gd)) + B;
@@ -646,15 +640,13 @@ __device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p
   }
   T F[3] = {T(0), T(0), T(0)};
   const bool force = p.has_force != 0;
-  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
-  const T inv = T(1) / rho0;
-  // u0 without the Guo half force (odd parts), u with it (Eq. density)
-  const T u0[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
   if (force) {
     F[0] = T(p.F[0]); F[1] = T(p.F[1]); F[2] = T(p.F[2]);
     jx += T(0.5) * F[0]; jy += T(0.5) * F[1]; jz += T(0.5) * F[2];
   }
-  const T u[3] = {force ? jx * inv : u0[0], force ? jy * inv : u0[1], L::D == 3 && force ? jz * inv : u0[2]};
+  const T rho0 = p.incompressible ? T(1) : T(1) + drho;
+  const T inv = T(1) / rho0;
+  const T u[3] = {jx * inv, jy * inv, L::D == 3 ? jz * inv : T(0)};
   const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T base = drho - T(1.5) * rho0 * usq;
   const T k45 = T(4.5) * rho0, k3 = T(3) * rho0;
@@ -677,9 +669,7 @@ __device__ __forceinline__ void collide_mrt(T (&h)[L::Q], const CollideParams& p
       Gd[k] = w * T(3) * cF;
     }
     gs[k] = s[k] - T(2) * w * fma(k45, cu * cu, base) + Gs[k];
-    // odd part: the F/2 of h^eq- and G-/2 cancel, so g- needs only the
-    // momentum without the half force
-    gd[k] = dd[k] - T(2) * w * k3 * cdot<L, T>(q, u0);
+    gd[k] = dd[k] - T(2) * w * k3 * cu + Gd[k];
   }
   T d[L::Q];
   mrt_forward_pairs<L, T>(g0, gs, gd, d, p, std::make_integer_sequence<int, L::Q>{});

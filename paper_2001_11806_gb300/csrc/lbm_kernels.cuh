@@ -329,10 +329,20 @@ __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, st
 }
 
 // ------------------------------------------------------------------- sweep
+// Resident blocks per SM asked of the compiler: the light operators (SRT,
+// TRT, their Smagorinsky variants, MRT with one higher-order rate) in 32-bit
+// arithmetic fit 56 registers, so 9 blocks of 128 threads (36 warps); the
+// rarely used Guo-force branch must not push the common path past that.
+template <class ST, int OP>
+constexpr int sweep_min_blocks() {
+  const bool light = OP == OP_SRT || OP == OP_TRT || OP == OP_SRT_LES || OP == OP_TRT_LES || OP == OP_MRT3;
+  return (light && sizeof(typename ST::T) == 4) ? 9 : 1;
+}
+
 // Fully periodic domains without flags: one thread per cell, 128-thread
 // blocks along x, grid (nx/128, ny, nz).
 template <class L, class ST, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(kBlockX, sweep_min_blocks<ST, OP>()) k_sweep(const SweepArgs a) {
   using T = typename ST::T;
   using S = typename ST::S;
   constexpr bool DH = dom_h<ST, OP>();
@@ -719,7 +729,7 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
 }
 
 template <class L, class ST, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
+__global__ void __launch_bounds__(kBlockX, sweep_min_blocks<ST, OP>()) k_sweep_list(const SweepArgs a) {
   sweep_list<L, ST, OP, KIND, false>(a);
 }
 

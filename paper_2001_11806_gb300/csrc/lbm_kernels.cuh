@@ -86,6 +86,7 @@ struct SweepArgs {
   int n_main, n_wrap;
   int boundary_mode;  // LBM_BOUNDARY_SEPARATE: the sweep streams every link as fluid
   int special_wrap;   // list builder: cells with inlet/outlet links go to the second launch
+  int list_ahead;     // main list launch: distance, in entries, of the L2 prefetch of entries
   // masked sweeps: element offsets, relative to the cell and to the stream of
   // the lower slot of the pair (q, qbar), of the population direction q
   // reads (lf: fluid link, lb: boundary link) and writes (sf, sb: fluid or
@@ -329,20 +330,22 @@ __device__ __forceinline__ void collide(T (&v)[L::Q], const CollideParams& p, st
 }
 
 // ------------------------------------------------------------------- sweep
-// Resident blocks per SM asked of the compiler: the light operators (SRT,
-// TRT, their Smagorinsky variants, MRT with one higher-order rate) in 32-bit
-// arithmetic fit 56 registers, so 9 blocks of 128 threads (36 warps); the
-// rarely used Guo-force branch must not push the common path past that.
+// The light operators (SRT, TRT, their Smagorinsky variants, MRT with one
+// higher-order rate) in 32-bit arithmetic fit 56 registers: their kernels are
+// compiled for 9 resident blocks of 128 threads (36 warps) per SM, so that
+// the rarely used Guo-force branch cannot push the common path past that.
+// The other operators keep the compiler's own register choice.
+constexpr int kLightBlocks = 9;
 template <class ST, int OP>
-constexpr int sweep_min_blocks() {
-  const bool light = OP == OP_SRT || OP == OP_TRT || OP == OP_SRT_LES || OP == OP_TRT_LES || OP == OP_MRT3;
-  return (light && sizeof(typename ST::T) == 4) ? 9 : 1;
+constexpr bool light_op() {
+  return (OP == OP_SRT || OP == OP_TRT || OP == OP_SRT_LES || OP == OP_TRT_LES || OP == OP_MRT3) &&
+         sizeof(typename ST::T) == 4;
 }
 
 // Fully periodic domains without flags: one thread per cell, 128-thread
 // blocks along x, grid (nx/128, ny, nz).
 template <class L, class ST, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX, sweep_min_blocks<ST, OP>()) k_sweep(const SweepArgs a) {
+__device__ __forceinline__ void sweep_dense(const SweepArgs& a) {
   using T = typename ST::T;
   using S = typename ST::S;
   constexpr bool DH = dom_h<ST, OP>();
@@ -433,6 +436,15 @@ __global__ void __launch_bounds__(kBlockX, sweep_min_blocks<ST, OP>()) k_sweep(c
       }
     }
   }
+}
+
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX) k_sweep(const SweepArgs a) {
+  sweep_dense<L, ST, OP, KIND>(a);
+}
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX, kLightBlocks) k_sweep_light(const SweepArgs a) {
+  sweep_dense<L, ST, OP, KIND>(a);
 }
 
 __device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& x, int& y, int& z) {
@@ -550,16 +562,14 @@ __device__ __forceinline__ uint2 reload_entry(const uint2* p) {
 // Sweep over list[0, n_main) (WRAP = false: every neighbour access is the
 // cell's own index plus a fixed offset) or over list[n_main, n_main + n_wrap)
 // (WRAP = true: neighbour indices from the coordinates, with wrapping).
+// One list entry (cell, link-mask word) at list position i.
 template <class L, class ST, int OP, int KIND, bool WRAP>
-__device__ __forceinline__ void sweep_list(const SweepArgs& a) {
+__device__ __forceinline__ void sweep_list(const SweepArgs& a, const uint2 entry, const int i) {
   using T = typename ST::T;
   using S = typename ST::S;
   constexpr bool DH = dom_h<ST, OP>();
   using D = Dom<ST, DH>;
   constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (WRAP ? a.n_wrap : a.n_main)) return;
-  const uint2 entry = a.list[WRAP ? a.n_main + i : i];
   const int cell = int(entry.x);
   const uint32_t mask = entry.y;
   T v[L::Q];
@@ -675,9 +685,7 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
   } else {
     // the entry is read again (a cache hit) rather than held across the
     // collision
-    int tx;
-    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
-    const uint2 es = reload_entry(a.list + blockIdx.x * blockDim.x + tx);
+    const uint2 es = reload_entry(a.list + i);
     const int cs = int(es.x);
     const uint32_t ms = es.y;
 #pragma unroll
@@ -698,9 +706,7 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
     // p = qbar); the inlet and outlet ones are stored again with their own
     // value B_p(P(x)) into the same slot.  After the stores, so that the
     // common path carries none of this.
-    int tx;
-    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
-    const uint2 es = reload_entry(a.list + blockIdx.x * blockDim.x + tx);
+    const uint2 es = reload_entry(a.list + i);
     if (es.y & MASK_SPECIAL) {
       const int cs = int(es.x);
       int x, y, z;
@@ -728,9 +734,27 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a) {
   }
 }
 
+// Main list launch, one entry per thread.  Each thread first asks the L2 to
+// fetch the entry that a block about one and a half resident grids later
+// will need (SweepArgs::list_ahead entries ahead), so that by the time that
+// block starts, its dependent entry load hits the L2 instead of DRAM; the
+// prefetch holds no register and nothing waits for it.
 template <class L, class ST, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX, sweep_min_blocks<ST, OP>()) k_sweep_list(const SweepArgs a) {
-  sweep_list<L, ST, OP, KIND, false>(a);
+__device__ __forceinline__ void sweep_list_main(const SweepArgs& a) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned ahead = i + unsigned(a.list_ahead);  // n_main < 2^31, list_ahead < 2^30: no wrap
+  if ((threadIdx.x & 15) == 0 && ahead < unsigned(a.n_main))
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.list + ahead));
+  if (i < unsigned(a.n_main)) sweep_list<L, ST, OP, KIND, false>(a, a.list[i], int(i));
+}
+
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX) k_sweep_list(const SweepArgs a) {
+  sweep_list_main<L, ST, OP, KIND>(a);
+}
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX, kLightBlocks) k_sweep_list_light(const SweepArgs a) {
+  sweep_list_main<L, ST, OP, KIND>(a);
 }
 
 // The main list sweep of D3Q19 with 16-bit storage under SRT, TRT and
@@ -751,12 +775,13 @@ constexpr bool list_capped() {
 
 template <class L, class ST, int OP, int KIND>
 __global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArgs a) {
-  sweep_list<L, ST, OP, KIND, false>(a);
+  sweep_list_main<L, ST, OP, KIND>(a);
 }
 
 template <class L, class ST, int OP, int KIND>
 __global__ void __launch_bounds__(kBlockX) k_sweep_list_wrap(const SweepArgs a) {
-  sweep_list<L, ST, OP, KIND, true>(a);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n_wrap) sweep_list<L, ST, OP, KIND, true>(a, a.list[a.n_main + i], a.n_main + i);
 }
 
 // Separate boundary kernel of the two-grid pull (LBM_BOUNDARY_SEPARATE):
@@ -1351,15 +1376,37 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
     }
   }
   if (!bnd) {
-    k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
+    if constexpr (light_op<ST, OP>())
+      k_sweep_light<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
+    else
+      k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
     return cudaGetLastError();
   }
   if (a.n_main > 0) {
+    // entry prefetch distance: one and a half times the threads resident at
+    // once (blocks per SM from the occupancy calculator, per instantiation)
+    static int resident = 0;
+    if (resident == 0) {
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if constexpr (list_capped<L, ST, OP>())
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_capped<L, ST, OP, KIND>, kBlockX, 0);
+      else if constexpr (light_op<ST, OP>())
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_light<L, ST, OP, KIND>, kBlockX, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list<L, ST, OP, KIND>, kBlockX, 0);
+      resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * kBlockX;
+    }
+    SweepArgs b = a;
+    b.list_ahead = resident + resident / 2;
     const int nb = (a.n_main + kBlockX - 1) / kBlockX;
     if constexpr (list_capped<L, ST, OP>())
-      k_sweep_list_capped<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(a);
+      k_sweep_list_capped<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
+    else if constexpr (light_op<ST, OP>())
+      k_sweep_list_light<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
     else
-      k_sweep_list<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(a);
+      k_sweep_list<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -695,7 +695,8 @@ def main():
     ap.add_argument("--size", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    # run one variant workload alone (name substring), e.g. to profile it
+    # run one variant workload alone (name substring), e.g. to profile it;
+    # "adjoint" runs the adjoint step and the whole gradient with T = --steps
     ap.add_argument("--variant", default=None)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -704,6 +705,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         peak = measured_peak()[0]
+        if args.variant == "adjoint":
+            # the adjoint step and the whole gradient, with T = --steps
+            for v in run_adjoint(torch.device("cuda:0"), peak, T=args.steps):
+                print(json.dumps(v))
+            return 0
         for v in run_variants(torch.device("cuda:0"), peak, only=args.variant, steps_override=args.steps,
                               warmup=args.warmup):
             print(json.dumps(v))

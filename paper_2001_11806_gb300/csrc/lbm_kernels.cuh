@@ -558,10 +558,49 @@ __device__ __forceinline__ uint2 reload_entry(const uint2* p) {
   asm volatile("ld.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
+// the same for two consecutive entries (p 16-byte aligned)
+__device__ __forceinline__ uint4 reload_entries2(const uint2* p) {
+  uint4 v;
+  asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
 
 // Sweep over list[0, n_main) (WRAP = false: every neighbour access is the
 // cell's own index plus a fixed offset) or over list[n_main, n_main + n_wrap)
 // (WRAP = true: neighbour indices from the coordinates, with wrapping).
+// Inlet and outlet links (x, p = qbar) of a cell swept by a single-array
+// pattern on the plain list path: the value B_p(P(x)) replaces the P_q(x)
+// the common stores wrote into the link's slot.  v: the cell's
+// post-collision populations in the register domain of D.
+template <class L, class ST, bool DH, int KIND>
+__device__ __forceinline__ void store_special_links(const SweepArgs& a, const typename ST::T (&v)[L::Q], int cs,
+                                                    uint32_t ms) {
+  using T = typename ST::T;
+  using S = typename ST::S;
+  using D = Dom<ST, DH>;
+  int x, y, z;
+  cell_coords(a.g, cs, x, y, z);
+  const OutletP op = outlet_params(a.cp);
+  T up[3];
+  post_velocity<L, T, DH>(v, op, up);
+#pragma unroll
+  for (int q = 1; q < L::Q; ++q) {
+    const int p = opp(q);
+    if ((ms >> p) & 1u) {
+      const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
+      if (t == L_INLET || t == L_OUTLET) {
+        const T val = t == L_INLET ? v[q] + ubb_term<L, T>(p, a.cp) : outlet_value<L, T, DH>(p, up, op);
+        if constexpr (KIND == K_AA_EVEN) {
+          pdf_st<S>(a, a.dstq[p], cs, D::store(val, L::w(q)));
+        } else {
+          const int lo = q < p ? q : p;
+          pdf_st<S>(a, a.dstq[lo], unsigned(cs) + a.sb[q], D::store(val, L::w(q)));
+        }
+      }
+    }
+  }
+}
+
 // One list entry (cell, link-mask word) at list position i.
 template <class L, class ST, int OP, int KIND, bool WRAP>
 __device__ __forceinline__ void sweep_list(const SweepArgs& a, const uint2 entry, const int i) {
@@ -707,30 +746,7 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a, const uint2 entry
     // value B_p(P(x)) into the same slot.  After the stores, so that the
     // common path carries none of this.
     const uint2 es = reload_entry(a.list + i);
-    if (es.y & MASK_SPECIAL) {
-      const int cs = int(es.x);
-      int x, y, z;
-      cell_coords(a.g, cs, x, y, z);
-      const OutletP op = outlet_params(a.cp);
-      T up[3];
-      post_velocity<L, T, DH>(v, op, up);
-#pragma unroll
-      for (int q = 1; q < L::Q; ++q) {
-        const int p = opp(q);
-        if ((es.y >> p) & 1u) {
-          const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
-          if (t == L_INLET || t == L_OUTLET) {
-            const T val = t == L_INLET ? v[q] + ubb_term<L, T>(p, a.cp) : outlet_value<L, T, DH>(p, up, op);
-            if constexpr (KIND == K_AA_EVEN) {
-              pdf_st<S>(a, a.dstq[p], cs, D::store(val, L::w(q)));
-            } else {
-              const int lo = q < p ? q : p;
-              pdf_st<S>(a, a.dstq[lo], unsigned(cs) + a.sb[q], D::store(val, L::w(q)));
-            }
-          }
-        }
-      }
-    }
+    if (es.y & MASK_SPECIAL) store_special_links<L, ST, DH, KIND>(a, v, int(es.x), es.y);
   }
 }
 
@@ -776,6 +792,126 @@ constexpr bool list_capped() {
 template <class L, class ST, int OP, int KIND>
 __global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArgs a) {
   sweep_list_main<L, ST, OP, KIND>(a);
+}
+
+// Main list launch for 16-bit storage with two consecutive list entries per
+// thread.  One 2-byte population per thread leaves too few bytes in flight to
+// cover the memory latency; with two cells per thread, their populations held
+// packed in one __half2 register per direction and collided one cell at a
+// time (as in k_sweep_h2), each thread keeps twice the bytes in flight for
+// about one collision's registers.  Addresses are per cell (the two cells need
+// not be neighbours).  Inlet and outlet links of the single-array patterns are
+// stored again after the common stores from the stored (binary16) values.
+template <class L, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX, 8) k_sweep_list_h2(const SweepArgs a) {
+  using ST = StF16S;
+  using T = float;
+  using S = __half;
+  constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
+  const unsigned n = unsigned(a.n_main);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned i0 = 2 * t;  // n < 2^31: no wrap
+  {
+    const unsigned ahead = i0 + unsigned(a.list_ahead);
+    if ((threadIdx.x & 7) == 0 && ahead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.list + ahead));
+  }
+  if (i0 >= n) return;
+  const bool has1 = i0 + 1 < n;
+  uint2 e0, e1;
+  if (has1) {
+    const uint4 ee = *reinterpret_cast<const uint4*>(a.list + i0);  // 16-byte aligned: i0 even
+    e0 = make_uint2(ee.x, ee.y);
+    e1 = make_uint2(ee.z, ee.w);
+  } else {
+    e0 = a.list[i0];
+    e1 = e0;
+  }
+  __half2 P[L::Q];
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    const __half* base;
+    unsigned i0q, i1q;
+    if constexpr (ESO) {
+      base = reinterpret_cast<const __half*>(a.srci[q]);
+      i0q = e0.x;
+      i1q = e1.x;
+    } else if constexpr (KIND == K_AA_EVEN) {
+      base = reinterpret_cast<const __half*>(a.srcq[q]);
+      i0q = e0.x;
+      i1q = e1.x;
+    } else {
+      const int lo = q < opp(q) ? q : opp(q);
+      base = reinterpret_cast<const __half*>(a.srcq[lo]);
+      i0q = e0.x + (((e0.y >> q) & 1u) ? a.lb[q] : a.lf[q]);
+      i1q = e1.x + (((e1.y >> q) & 1u) ? a.lb[q] : a.lf[q]);
+    }
+    P[q] = __halves2half2(pdf_ld<S>(a, base, i0q), pdf_ld<S>(a, base, i1q));
+  }
+  {
+    T v[L::Q];
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
+    collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__float2half_rn(v[q]), __high2half(P[q]));
+  }
+  {
+    T v[L::Q];
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
+    collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__low2half(P[q]), __float2half_rn(v[q]));
+  }
+  // entries again (cache hits), not held across the collisions
+  uint2 s0, s1;
+  {
+    uint4 ee;
+    if (has1) {
+      ee = reload_entries2(a.list + i0);
+    } else {
+      const uint2 e = reload_entry(a.list + i0);
+      ee = make_uint4(e.x, e.y, 0u, 0u);
+    }
+    s0 = make_uint2(ee.x, ee.y);
+    s1 = make_uint2(ee.z, ee.w);
+  }
+#pragma unroll
+  for (int q = 0; q < L::Q; ++q) {
+    __half* base;
+    unsigned i0q, i1q;
+    if constexpr (KIND == K_PULL) {
+      base = reinterpret_cast<__half*>(a.dstq[q]);
+      i0q = s0.x;
+      i1q = s1.x;
+    } else if constexpr (KIND == K_AA_EVEN) {
+      base = reinterpret_cast<__half*>(a.dstq[opp(q)]);
+      i0q = s0.x;
+      i1q = s1.x;
+    } else {
+      const int p = opp(q);
+      const int lo = q < p ? q : p;
+      base = reinterpret_cast<__half*>(a.dstq[lo]);
+      i0q = s0.x + (((s0.y >> p) & 1u) ? a.sb[q] : a.sf[q]);
+      i1q = s1.x + (((s1.y >> p) & 1u) ? a.sb[q] : a.sf[q]);
+    }
+    pdf_st<S>(a, base, i0q, __low2half(P[q]));
+    if (has1) pdf_st<S>(a, base, i1q, __high2half(P[q]));
+  }
+  if constexpr (KIND != K_PULL) {
+    if (s0.y & MASK_SPECIAL) {
+      T v[L::Q];
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
+      store_special_links<L, ST, true, KIND>(a, v, int(s0.x), s0.y);
+    }
+    if (has1 && (s1.y & MASK_SPECIAL)) {
+      T v[L::Q];
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
+      store_special_links<L, ST, true, KIND>(a, v, int(s1.x), s1.y);
+    }
+  }
 }
 
 template <class L, class ST, int OP, int KIND>
@@ -1391,7 +1527,7 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if constexpr (list_capped<L, ST, OP>())
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_capped<L, ST, OP, KIND>, kBlockX, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_h2<L, OP, KIND>, kBlockX, 0);
       else if constexpr (light_op<ST, OP>())
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_light<L, ST, OP, KIND>, kBlockX, 0);
       else
@@ -1399,10 +1535,11 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * kBlockX;
     }
     SweepArgs b = a;
-    b.list_ahead = resident + resident / 2;
+    // in entries: the pair kernel takes two per thread
+    b.list_ahead = (list_capped<L, ST, OP>() ? 2 : 1) * (resident + resident / 2);
     const int nb = (a.n_main + kBlockX - 1) / kBlockX;
     if constexpr (list_capped<L, ST, OP>())
-      k_sweep_list_capped<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
+      k_sweep_list_h2<L, OP, KIND><<<(a.n_main + 2 * kBlockX - 1) / (2 * kBlockX), kBlockX, 0, s>>>(b);
     else if constexpr (light_op<ST, OP>())
       k_sweep_list_light<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
     else

@@ -482,7 +482,7 @@ def _rel_errors(fields, ref, mask=None):
             "u": float(max(np.linalg.norm(v[a] - u64[a]) / np.linalg.norm(u64[a]) for a in range(v.shape[0])))}
 
 
-def run_accuracy(device):
+def run_accuracy(device, cumulant_steps=100):
     """FP32 and FP16-shifted storage against an FP64 run of the same kernels
     (the secondary reference; the FP64 oracle is too slow at these sizes).
     Relative L2 of rho - 1 and of u (fluid cells), kinetic energy ratios.
@@ -490,9 +490,10 @@ def run_accuracy(device):
     - D3Q19 MRT channel 512x128x128 (walls, inlet 0.05, outlet, obstacles),
       2000 steps from rest, AA;
     - D3Q27 cumulant 384^3 TGV u0 = 0.05: FP32 kinetic-energy decay over 5000
-      steps, and FP32 against FP64 after 100 steps (FP64 cumulant arithmetic
-      runs at about 0.5 GLUPS on this part, so 5000 FP64 steps would take
-      minutes)."""
+      steps, and FP32 against FP64 after `cumulant_steps` steps (100 by
+      default: FP64 cumulant arithmetic runs at about 0.5 GLUPS on this part,
+      so the 5000 steps of the workload take about ten minutes, which
+      --accuracy-only --cumulant-steps 5000 runs on its own)."""
     import torch
 
     from paper_2001_11806_gb300 import inputs
@@ -552,12 +553,12 @@ def run_accuracy(device):
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    fields, ke = run(kw, rho, u, 100, ["f64", "f32"])
+    fields, ke = run(kw, rho, u, cumulant_steps, ["f64", "f32"])
     out.append({"workload": "D3Q27 cumulant 384^3 TGV u0 = 0.05, omega 1.95, AA",
                 "ke_ratio_f32": decay,
-                "f32_vs_f64_after_100_steps": dict(_rel_errors(fields["f32"], fields["f64"]),
-                                                   ke_ratio_f64=round(float(ke["f64"]), 8),
-                                                   ke_ratio_f32=round(float(ke["f32"]), 8))})
+                f"f32_vs_f64_after_{cumulant_steps}_steps": dict(_rel_errors(fields["f32"], fields["f64"]),
+                                                                 ke_ratio_f64=round(float(ke["f64"]), 8),
+                                                                 ke_ratio_f32=round(float(ke["f32"]), 8))})
     return out
 
 
@@ -656,7 +657,7 @@ def run_gpu(args, world, rank, local):
         # spawned processes only: this process has used the GPU already
         cpu_mlups, cpu_steps, cpu_dt = oracle_parallel_run(cpu_cores, 10 ** 9, 1, 12.0, CPU_SIDE)
     variants = None if args.no_variants else run_variants(device, peak)
-    accuracy = None if args.no_variants else run_accuracy(device)
+    accuracy = None if args.no_variants else run_accuracy(device, args.cumulant_steps)
     line = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
@@ -695,12 +696,20 @@ def main():
     ap.add_argument("--size", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    # the FP32/FP16 accuracy runs alone; the cumulant's FP32-vs-FP64 length
+    ap.add_argument("--accuracy-only", action="store_true")
+    ap.add_argument("--cumulant-steps", type=int, default=100)
     # run one variant workload alone (name substring), e.g. to profile it;
     # "adjoint" runs the adjoint step and the whole gradient with T = --steps
     ap.add_argument("--variant", default=None)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.accuracy_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"accuracy": run_accuracy(torch.device("cuda:0"), args.cumulant_steps)}))
+        return 0
     if args.variant is not None:
         import torch
         torch.cuda.set_device(0)

@@ -558,12 +558,7 @@ __device__ __forceinline__ uint2 reload_entry(const uint2* p) {
   asm volatile("ld.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
-// the same for two consecutive entries (p 16-byte aligned)
-__device__ __forceinline__ uint4 reload_entries2(const uint2* p) {
-  uint4 v;
-  asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-  return v;
-}
+
 
 // Sweep over list[0, n_main) (WRAP = false: every neighbour access is the
 // cell's own index plus a fixed offset) or over list[n_main, n_main + n_wrap)
@@ -794,124 +789,132 @@ __global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArg
   sweep_list_main<L, ST, OP, KIND>(a);
 }
 
-// Main list launch for 16-bit storage with two consecutive list entries per
-// thread.  One 2-byte population per thread leaves too few bytes in flight to
-// cover the memory latency; with two cells per thread, their populations held
-// packed in one __half2 register per direction and collided one cell at a
-// time (as in k_sweep_h2), each thread keeps twice the bytes in flight for
-// about one collision's registers.  Addresses are per cell (the two cells need
-// not be neighbours).  Inlet and outlet links of the single-array patterns are
-// stored again after the common stores from the stored (binary16) values.
-template <class L, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX, 8) k_sweep_list_h2(const SweepArgs a) {
-  using ST = StF16S;
-  using T = float;
-  using S = __half;
+// ------------------------------------------ pipelined list sweep (32-bit)
+// Main list launch of the light operators with 32-bit storage.  The loads of
+// a list sweep are gathers, so a thread's population loads must wait for its
+// entry and then hold a register each until they land; that leaves too few
+// bytes in flight to cover the memory latency (ncu: 67 % of DRAM bandwidth,
+// long-scoreboard stalls).  Here a persistent grid walks the list in tiles
+// of 128 entries per block, and each thread copies the populations of its
+// next cell into shared memory with cp.async (4-byte asynchronous copies
+// that hold no register) while it collides and stores the current one: a
+// two-stage pipeline per thread, [stage][q][thread] in shared memory, read
+// back only by the thread that issued the copies (so no block barrier), and
+// the entries are loaded two tiles ahead.
+constexpr int kPipeStages = 2;
+
+template <class L, class ST>
+constexpr size_t pipe_smem_bytes() {
+  return size_t(kPipeStages) * L::Q * kBlockX * sizeof(typename ST::S);
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The addresses a cell's populations are read from on the plain list path
+// (see sweep_list), as copies into its stage slots.
+template <class L, class ST, int KIND>
+__device__ __forceinline__ void pipe_issue(const SweepArgs& a, typename ST::S* slot, uint2 e) {
+  using S = typename ST::S;
   constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
-  const unsigned n = unsigned(a.n_main);
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned i0 = 2 * t;  // n < 2^31: no wrap
-  {
-    const unsigned ahead = i0 + unsigned(a.list_ahead);
-    if ((threadIdx.x & 7) == 0 && ahead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.list + ahead));
-  }
-  if (i0 >= n) return;
-  const bool has1 = i0 + 1 < n;
-  uint2 e0, e1;
-  if (has1) {
-    const uint4 ee = *reinterpret_cast<const uint4*>(a.list + i0);  // 16-byte aligned: i0 even
-    e0 = make_uint2(ee.x, ee.y);
-    e1 = make_uint2(ee.z, ee.w);
-  } else {
-    e0 = a.list[i0];
-    e1 = e0;
-  }
-  __half2 P[L::Q];
+  const int cell = int(e.x);
 #pragma unroll
   for (int q = 0; q < L::Q; ++q) {
-    const __half* base;
-    unsigned i0q, i1q;
+    const S* src;
     if constexpr (ESO) {
-      base = reinterpret_cast<const __half*>(a.srci[q]);
-      i0q = e0.x;
-      i1q = e1.x;
+      src = reinterpret_cast<const S*>(a.srci[q]) + cell;
     } else if constexpr (KIND == K_AA_EVEN) {
-      base = reinterpret_cast<const __half*>(a.srcq[q]);
-      i0q = e0.x;
-      i1q = e1.x;
+      src = reinterpret_cast<const S*>(a.srcq[q]) + cell;
     } else {
       const int lo = q < opp(q) ? q : opp(q);
-      base = reinterpret_cast<const __half*>(a.srcq[lo]);
-      i0q = e0.x + (((e0.y >> q) & 1u) ? a.lb[q] : a.lf[q]);
-      i1q = e1.x + (((e1.y >> q) & 1u) ? a.lb[q] : a.lf[q]);
+      src = reinterpret_cast<const S*>(a.srcq[lo]) + (unsigned(cell) + (((e.y >> q) & 1u) ? a.lb[q] : a.lf[q]));
     }
-    P[q] = __halves2half2(pdf_ld<S>(a, base, i0q), pdf_ld<S>(a, base, i1q));
-  }
-  {
-    T v[L::Q];
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
-    collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__float2half_rn(v[q]), __high2half(P[q]));
-  }
-  {
-    T v[L::Q];
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
-    collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__low2half(P[q]), __float2half_rn(v[q]));
-  }
-  // entries again (cache hits), not held across the collisions
-  uint2 s0, s1;
-  {
-    uint4 ee;
-    if (has1) {
-      ee = reload_entries2(a.list + i0);
-    } else {
-      const uint2 e = reload_entry(a.list + i0);
-      ee = make_uint4(e.x, e.y, 0u, 0u);
+#ifdef LBM_DEBUG_BOUNDS
+    if (!pdf_in_bounds<S>(a, src)) {
+      atomicOr(a.bounds_flag, 1u);
+      continue;
     }
-    s0 = make_uint2(ee.x, ee.y);
-    s1 = make_uint2(ee.z, ee.w);
+#endif
+    cp_async4(slot + q * kBlockX, src);
   }
-#pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    __half* base;
-    unsigned i0q, i1q;
-    if constexpr (KIND == K_PULL) {
-      base = reinterpret_cast<__half*>(a.dstq[q]);
-      i0q = s0.x;
-      i1q = s1.x;
-    } else if constexpr (KIND == K_AA_EVEN) {
-      base = reinterpret_cast<__half*>(a.dstq[opp(q)]);
-      i0q = s0.x;
-      i1q = s1.x;
-    } else {
-      const int p = opp(q);
-      const int lo = q < p ? q : p;
-      base = reinterpret_cast<__half*>(a.dstq[lo]);
-      i0q = s0.x + (((s0.y >> p) & 1u) ? a.sb[q] : a.sf[q]);
-      i1q = s1.x + (((s1.y >> p) & 1u) ? a.sb[q] : a.sf[q]);
-    }
-    pdf_st<S>(a, base, i0q, __low2half(P[q]));
-    if (has1) pdf_st<S>(a, base, i1q, __high2half(P[q]));
-  }
-  if constexpr (KIND != K_PULL) {
-    if (s0.y & MASK_SPECIAL) {
+}
+
+template <class L, class ST, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX, kLightBlocks) k_sweep_list_pipe(const SweepArgs a) {
+  using T = typename ST::T;
+  using S = typename ST::S;
+  static_assert(sizeof(S) == 4, "4-byte asynchronous copies");
+  constexpr bool DH = dom_h<ST, OP>();
+  using D = Dom<ST, DH>;
+  extern __shared__ float4 pipe_smem[];
+  S* stage = reinterpret_cast<S*>(pipe_smem);  // [kPipeStages][Q][kBlockX]
+  const unsigned n = unsigned(a.n_main);
+  const unsigned tiles = (n + kBlockX - 1) / kBlockX;
+  const unsigned tid = threadIdx.x;
+  // tiles of this block: blockIdx.x, + gridDim.x, ...; entries beyond n are
+  // invalid (the last tile may be partial), tiles beyond `tiles` do not run
+  unsigned t0 = blockIdx.x;
+  unsigned t1 = t0 + gridDim.x;
+  auto entry_at = [&](unsigned t, bool& valid) {
+    const unsigned i = t * kBlockX + tid;  // < 2^31 + 2^8 * grid: no wrap
+    valid = t < tiles && i < n;
+    return valid ? a.list[i] : make_uint2(0u, 0u);
+  };
+  bool v0, v1;
+  uint2 e0 = entry_at(t0, v0);
+  uint2 e1 = entry_at(t1, v1);
+  if (v0) pipe_issue<L, ST, KIND>(a, stage + tid, e0);
+  cp_async_commit();
+  int st = 0;
+  while (t0 < tiles) {
+    // copies of the next tile, and the entry of the one after it
+    if (v1) pipe_issue<L, ST, KIND>(a, stage + (st ^ 1) * L::Q * kBlockX + tid, e1);
+    cp_async_commit();
+    bool v2;
+    const unsigned t2 = t1 + gridDim.x;
+    const uint2 e2 = entry_at(t2, v2);
+    cp_async_wait_prev();
+    if (v0) {
+      const S* slot = stage + st * L::Q * kBlockX + tid;
       T v[L::Q];
 #pragma unroll
-      for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
-      store_special_links<L, ST, true, KIND>(a, v, int(s0.x), s0.y);
-    }
-    if (has1 && (s1.y & MASK_SPECIAL)) {
-      T v[L::Q];
+      for (int q = 0; q < L::Q; ++q) v[q] = D::load(slot[q * kBlockX], L::w(q));
+      collide<L, T, DH>(v, a.cp, std::integral_constant<int, OP>{});
+      const int cs = int(e0.x);
+      const uint32_t ms = e0.y;
+      if constexpr (KIND == K_PULL) {
 #pragma unroll
-      for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
-      store_special_links<L, ST, true, KIND>(a, v, int(s1.x), s1.y);
+        for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[q], cs, D::store(v[q], L::w(q)));
+      } else if constexpr (KIND == K_AA_EVEN) {
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[opp(q)], cs, D::store(v[q], L::w(q)));
+      } else {
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) {
+          const int p = opp(q);
+          const int lo = q < p ? q : p;
+          const unsigned idx = unsigned(cs) + (((ms >> p) & 1u) ? a.sb[q] : a.sf[q]);
+          pdf_st<S>(a, a.dstq[lo], idx, D::store(v[q], L::w(q)));
+        }
+      }
+      if constexpr (KIND != K_PULL) {
+        if (ms & MASK_SPECIAL) store_special_links<L, ST, DH, KIND>(a, v, cs, ms);
+      }
     }
+    t0 = t1;
+    t1 = t2;
+    e0 = e1;
+    e1 = e2;
+    v0 = v1;
+    v1 = v2;
+    st ^= 1;
   }
+  cp_async_wait_all();
 }
 
 template <class L, class ST, int OP, int KIND>
@@ -1518,7 +1521,25 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
     return cudaGetLastError();
   }
-  if (a.n_main > 0) {
+  constexpr bool PIPE = light_op<ST, OP>() && sizeof(typename ST::S) == 4;
+  if constexpr (PIPE) {
+    if (a.n_main > 0) {
+      // persistent grid: the blocks resident at once with the pipeline's
+      // shared memory (occupancy calculator, per instantiation)
+      static int resident_blocks = 0;
+      constexpr size_t smem = pipe_smem_bytes<L, ST>();
+      if (resident_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_pipe<L, ST, OP, KIND>, kBlockX, smem);
+        resident_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+      }
+      const int tiles = (a.n_main + kBlockX - 1) / kBlockX;
+      const int nb = tiles < resident_blocks ? tiles : resident_blocks;
+      k_sweep_list_pipe<L, ST, OP, KIND><<<nb, kBlockX, smem, s>>>(a);
+    }
+  } else if (a.n_main > 0) {
     // entry prefetch distance: one and a half times the threads resident at
     // once (blocks per SM from the occupancy calculator, per instantiation)
     static int resident = 0;
@@ -1527,7 +1548,7 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if constexpr (list_capped<L, ST, OP>())
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_h2<L, OP, KIND>, kBlockX, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_capped<L, ST, OP, KIND>, kBlockX, 0);
       else if constexpr (light_op<ST, OP>())
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_light<L, ST, OP, KIND>, kBlockX, 0);
       else
@@ -1535,11 +1556,10 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * kBlockX;
     }
     SweepArgs b = a;
-    // in entries: the pair kernel takes two per thread
-    b.list_ahead = (list_capped<L, ST, OP>() ? 2 : 1) * (resident + resident / 2);
+    b.list_ahead = resident + resident / 2;
     const int nb = (a.n_main + kBlockX - 1) / kBlockX;
     if constexpr (list_capped<L, ST, OP>())
-      k_sweep_list_h2<L, OP, KIND><<<(a.n_main + 2 * kBlockX - 1) / (2 * kBlockX), kBlockX, 0, s>>>(b);
+      k_sweep_list_capped<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
     else if constexpr (light_op<ST, OP>())
       k_sweep_list_light<L, ST, OP, KIND><<<nb, kBlockX, 0, s>>>(b);
     else

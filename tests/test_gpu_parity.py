@@ -614,3 +614,17 @@ def test_injected_allocation_failure_with_flags():
 def _lib_last_error(sim):
     from paper_2001_11806_gb300 import _lib
     return _lib.lib().lbm_last_error(sim.ctx)
+
+
+@pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
+@pytest.mark.parametrize("shape", [(150, 5, 4), (149, 5, 3)])
+def test_f16_list_sweep_even_and_odd_cell_counts(pattern, shape):
+    """The pipelined list sweep of 16-bit storage copies each population in
+    its aligned 4-byte word, which needs an even cell count; an odd count
+    takes the one-entry list kernel.  Both against the oracle, element-wise."""
+    fl = _flags(shape)
+    r = run_pair("D3Q19", "trt", "f16s", pattern, shape, 4, periodic=(False, False, True), flags=fl,
+                 u_wall=(0.05, 0.01, 0.0))
+    ef, er, eu = _errs(r)
+    assert ef < 5e-3 and er < 5e-3 and eu < 5e-3, (ef, er, eu)
+    assert_f16_elementwise(*r["f"], r["lat"].w)

@@ -789,162 +789,6 @@ __global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArg
   sweep_list_main<L, ST, OP, KIND>(a);
 }
 
-// ------------------------------------------------- pipelined list sweep
-// Main list launch of the light operators with 32- or 16-bit storage.  The loads of
-// a list sweep are gathers, so a thread's population loads must wait for its
-// entry and then hold a register each until they land; that leaves too few
-// bytes in flight to cover the memory latency (ncu: 67 % of DRAM bandwidth,
-// long-scoreboard stalls).  Here a persistent grid walks the list in tiles
-// of 128 entries per block, and each thread copies the populations of its
-// next cell into shared memory with cp.async (4-byte asynchronous copies
-// that hold no register) while it collides and stores the current one: a
-// two-stage pipeline per thread, [stage][q][thread] in shared memory, read
-// back only by the thread that issued the copies (so no block barrier), and
-// the entries are loaded two tiles ahead.  A copy moves at least 4 aligned
-// bytes, so a 16-bit population travels in the aligned 4-byte word that holds
-// it and is picked out of the word afterwards.
-#ifndef LBM_PIPE_STAGES
-#define LBM_PIPE_STAGES 3
-#endif
-constexpr int kPipeStages = LBM_PIPE_STAGES;
-
-// shared memory of a block: [stage][q][thread] population words, then
-// [stage][thread] list entries
-template <class L, class ST>
-constexpr size_t pipe_smem_bytes() {
-  return size_t(kPipeStages) * kBlockX * (L::Q * 4 + sizeof(uint2));
-}
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-// wait until at most N of this thread's copy groups are in flight
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// The address population q of a cell is read from on the plain list path
-// (see sweep_list).
-template <class L, class ST, int KIND>
-__device__ __forceinline__ const typename ST::S* pipe_src(const SweepArgs& a, int q, uint2 e) {
-  using S = typename ST::S;
-  constexpr bool ESO = KIND == K_ESO_EVEN || KIND == K_ESO_ODD;
-  const int cell = int(e.x);
-  if constexpr (ESO) {
-    return reinterpret_cast<const S*>(a.srci[q]) + cell;
-  } else if constexpr (KIND == K_AA_EVEN) {
-    return reinterpret_cast<const S*>(a.srcq[q]) + cell;
-  } else {
-    const int lo = q < opp(q) ? q : opp(q);
-    return reinterpret_cast<const S*>(a.srcq[lo]) + (unsigned(cell) + (((e.y >> q) & 1u) ? a.lb[q] : a.lf[q]));
-  }
-}
-
-// Copies of a cell's populations into its stage slots (4-byte words).
-template <class L, class ST, int KIND>
-__device__ __forceinline__ void pipe_issue(const SweepArgs& a, uint32_t* slot, uint2 e) {
-  using S = typename ST::S;
-#pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    const S* src = pipe_src<L, ST, KIND>(a, q, e);
-#ifdef LBM_DEBUG_BOUNDS
-    if (!pdf_in_bounds<S>(a, src)) {
-      atomicOr(a.bounds_flag, 1u);
-      continue;
-    }
-#endif
-    const void* word = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
-    cp_async4(slot + q * kBlockX, word);
-  }
-}
-
-// Population q of a cell from its stage word.
-template <class L, class ST, int KIND>
-__device__ __forceinline__ typename ST::S pipe_value(const SweepArgs& a, const uint32_t* slot, int q, uint2 e) {
-  using S = typename ST::S;
-  const uint32_t w = slot[q * kBlockX];
-  if constexpr (sizeof(S) == 4) {
-    return __uint_as_float(w);
-  } else {
-    const bool hi = (reinterpret_cast<uintptr_t>(pipe_src<L, ST, KIND>(a, q, e)) & 2) != 0;
-    return __ushort_as_half(static_cast<unsigned short>(hi ? (w >> 16) : (w & 0xffffu)));
-  }
-}
-
-template <class L, class ST, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX, kLightBlocks) k_sweep_list_pipe(const SweepArgs a) {
-  using T = typename ST::T;
-  using S = typename ST::S;
-  constexpr bool DH = dom_h<ST, OP>();
-  constexpr int NS = kPipeStages;
-  using D = Dom<ST, DH>;
-  extern __shared__ float4 pipe_smem[];
-  uint32_t* words = reinterpret_cast<uint32_t*>(pipe_smem);                // [NS][Q][kBlockX]
-  uint2* ents = reinterpret_cast<uint2*>(words + NS * L::Q * kBlockX);    // [NS][kBlockX]
-  const unsigned n = unsigned(a.n_main);
-  const unsigned tiles = (n + kBlockX - 1) / kBlockX;
-  const unsigned tid = threadIdx.x;
-  // this block's k-th tile is blockIdx.x + k gridDim.x; an entry past n is
-  // invalid (the last tile may be partial)
-  auto entry_of = [&](unsigned k) {
-    const unsigned t = blockIdx.x + k * gridDim.x;  // < tiles + grid < 2^31: no wrap
-    const unsigned i = t * kBlockX + tid;
-    return (t < tiles && i < n) ? a.list[i] : make_uint2(0u, MASK_SOLID);
-  };
-  // copies of tile k into stage k % NS (nothing for an invalid entry), with
-  // the entry kept beside them for the collision and the stores
-  auto issue = [&](unsigned k, uint2 e) {
-    const int st = int(k % NS);
-    ents[st * kBlockX + tid] = e;
-    if (!(e.y & MASK_SOLID)) pipe_issue<L, ST, KIND>(a, words + st * L::Q * kBlockX + tid, e);
-    cp_async_commit();
-  };
-  uint2 e = entry_of(0);
-#pragma unroll
-  for (int k = 0; k < NS - 1; ++k) {
-    const uint2 en = entry_of(k + 1);
-    issue(k, e);
-    e = en;
-  }
-  // e: entry of tile NS - 1
-  for (unsigned k = 0; blockIdx.x + k * gridDim.x < tiles; ++k) {
-    const uint2 en = entry_of(k + NS);
-    issue(k + NS - 1, e);
-    e = en;
-    cp_async_wait<NS - 1>();  // tile k has landed
-    const int st = int(k % NS);
-    const uint2 ec = ents[st * kBlockX + tid];
-    if (ec.y & MASK_SOLID) continue;
-    const uint32_t* slot = words + st * L::Q * kBlockX + tid;
-    T v[L::Q];
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) v[q] = D::load(pipe_value<L, ST, KIND>(a, slot, q, ec), L::w(q));
-    collide<L, T, DH>(v, a.cp, std::integral_constant<int, OP>{});
-    const int cs = int(ec.x);
-    const uint32_t ms = ec.y;
-    if constexpr (KIND == K_PULL) {
-#pragma unroll
-      for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[q], cs, D::store(v[q], L::w(q)));
-    } else if constexpr (KIND == K_AA_EVEN) {
-#pragma unroll
-      for (int q = 0; q < L::Q; ++q) pdf_st<S>(a, a.dstq[opp(q)], cs, D::store(v[q], L::w(q)));
-    } else {
-#pragma unroll
-      for (int q = 0; q < L::Q; ++q) {
-        const int p = opp(q);
-        const int lo = q < p ? q : p;
-        const unsigned idx = unsigned(cs) + (((ms >> p) & 1u) ? a.sb[q] : a.sf[q]);
-        pdf_st<S>(a, a.dstq[lo], idx, D::store(v[q], L::w(q)));
-      }
-    }
-    if constexpr (KIND != K_PULL) {
-      if (ms & MASK_SPECIAL) store_special_links<L, ST, DH, KIND>(a, v, cs, ms);
-    }
-  }
-  cp_async_wait<0>();
-}
-
 template <class L, class ST, int OP, int KIND>
 __global__ void __launch_bounds__(kBlockX) k_sweep_list_wrap(const SweepArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1009,7 +853,7 @@ __global__ void __launch_bounds__(kBlockX) k_boundary_pull(const SweepArgs a, ty
 // register cost is one packed register per direction plus one collision.
 // Requires an even nx (x0 and every row start are then 4-byte aligned).
 template <class L, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
+__device__ __forceinline__ void sweep_h2(const SweepArgs& a) {
   using T = float;
   const int tp = blockIdx.x * blockDim.x + threadIdx.x;
   const int x0 = 2 * tp;
@@ -1150,6 +994,17 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
       }
     }
   }
+}
+
+template <class L, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
+  sweep_h2<L, OP, KIND>(a);
+}
+// SRT and TRT at 9 resident blocks (see light_op; the heavier light
+// operators spill at that register count with two cells per thread)
+template <class L, int OP, int KIND>
+__global__ void __launch_bounds__(kBlockX, kLightBlocks) k_sweep_h2_light(const SweepArgs a) {
+  sweep_h2<L, OP, KIND>(a);
 }
 
 // ------------------------------------------------------------- gather (FP64)
@@ -1538,7 +1393,10 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
     if (!bnd && (a.g.nx % 2) == 0) {
       Geom half = a.g;
       half.nx = a.g.nx / 2;
-      k_sweep_h2<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
+      if constexpr (OP == OP_SRT || OP == OP_TRT)
+        k_sweep_h2_light<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
+      else
+        k_sweep_h2<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
       return cudaGetLastError();
     }
   }
@@ -1549,34 +1407,7 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
     return cudaGetLastError();
   }
-  // 16-bit storage: only with an even cell count, so that every stream
-  // starts on a 4-byte boundary and each population's 4-byte word lies inside
-  // the array
-  constexpr bool PIPE = light_op<ST, OP>() && (sizeof(typename ST::S) == 4 || list_capped<L, ST, OP>());
-  if (PIPE && (sizeof(typename ST::S) == 4 || (a.g.N & 1) == 0)) {
-    if (a.n_main > 0) {
-      // persistent grid: the blocks resident at once with the pipeline's
-      // shared memory (occupancy calculator, per instantiation)
-      static int resident_blocks = 0;
-      constexpr size_t smem = pipe_smem_bytes<L, ST>();
-      if (resident_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if constexpr (PIPE) {
-          // as much shared memory as the SM allows, so that the blocks the
-          // calculator counts are resident at once (the grid is persistent)
-          cudaFuncSetAttribute(k_sweep_list_pipe<L, ST, OP, KIND>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_list_pipe<L, ST, OP, KIND>, kBlockX, smem);
-        }
-        resident_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-      }
-      const int tiles = (a.n_main + kBlockX - 1) / kBlockX;
-      const int nb = tiles < resident_blocks ? tiles : resident_blocks;
-      if constexpr (PIPE) k_sweep_list_pipe<L, ST, OP, KIND><<<nb, kBlockX, smem, s>>>(a);
-    }
-  } else if (a.n_main > 0) {
+  if (a.n_main > 0) {
     // entry prefetch distance: one and a half times the threads resident at
     // once (blocks per SM from the occupancy calculator, per instantiation)
     static int resident = 0;

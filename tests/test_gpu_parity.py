@@ -619,9 +619,9 @@ def _lib_last_error(sim):
 @pytest.mark.parametrize("pattern", ["pull", "aa", "eso"])
 @pytest.mark.parametrize("shape", [(150, 5, 4), (149, 5, 3)])
 def test_f16_list_sweep_even_and_odd_cell_counts(pattern, shape):
-    """The pipelined list sweep of 16-bit storage copies each population in
-    its aligned 4-byte word, which needs an even cell count; an odd count
-    takes the one-entry list kernel.  Both against the oracle, element-wise."""
+    """The FP16 list sweep (capped main launch) on even and odd cell counts,
+    so that the population streams start on 4-byte and on 2-byte
+    boundaries; against the oracle, element-wise."""
     fl = _flags(shape)
     r = run_pair("D3Q19", "trt", "f16s", pattern, shape, 4, periodic=(False, False, True), flags=fl,
                  u_wall=(0.05, 0.01, 0.0))

@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(kBlockX) k_boundary_pull(const SweepArgs a, ty
 // register cost is one packed register per direction plus one collision.
 // Requires an even nx (x0 and every row start are then 4-byte aligned).
 template <class L, int OP, int KIND>
-__device__ __forceinline__ void sweep_h2(const SweepArgs& a) {
+__global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
   using T = float;
   const int tp = blockIdx.x * blockDim.x + threadIdx.x;
   const int x0 = 2 * tp;
@@ -994,17 +994,6 @@ __device__ __forceinline__ void sweep_h2(const SweepArgs& a) {
       }
     }
   }
-}
-
-template <class L, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX) k_sweep_h2(const SweepArgs a) {
-  sweep_h2<L, OP, KIND>(a);
-}
-// SRT and TRT at 9 resident blocks (see light_op; the heavier light
-// operators spill at that register count with two cells per thread)
-template <class L, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX, kLightBlocks) k_sweep_h2_light(const SweepArgs a) {
-  sweep_h2<L, OP, KIND>(a);
 }
 
 // ------------------------------------------------------------- gather (FP64)
@@ -1393,10 +1382,7 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
     if (!bnd && (a.g.nx % 2) == 0) {
       Geom half = a.g;
       half.nx = a.g.nx / 2;
-      if constexpr (OP == OP_SRT || OP == OP_TRT)
-        k_sweep_h2_light<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
-      else
-        k_sweep_h2<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
+      k_sweep_h2<L, OP, KIND><<<sweep_grid(half), sweep_block(half), 0, s>>>(a);
       return cudaGetLastError();
     }
   }

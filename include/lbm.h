@@ -101,13 +101,19 @@ enum { LBM_PULL = 0, LBM_AA = 1, LBM_ESOTWIST = 2 };
 enum { LBM_BOUNDARY_IN_SWEEP = 0, LBM_BOUNDARY_SEPARATE = 1 };
 /* uint8 flag per cell; 0 = fluid.  A boundary link (x, q) takes its type from
  * the flag of its source cell x - c_q with precedence NOSLIP > INLET > OUTLET
- * (a non-zero flag with none of these bits counts as NOSLIP).  Sources outside
- * a non-periodic axis count as NOSLIP. */
-enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_INLET = 2, LBM_OUTLET = 4 };
+ * (a non-zero flag with none of these bits and without the GHOST bit counts as
+ * NOSLIP).  Sources outside a non-periodic axis count as NOSLIP.
+ * GHOST (without NOSLIP, INLET or OUTLET; other bits ignored): a ghost cell of
+ * a block partition (Sec. IV-D "Framework Integration"): it is not swept and
+ * its populations come from the neighbouring block (lbm_halo_unpack), and
+ * links from it stream like fluid links. */
+enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_INLET = 2, LBM_OUTLET = 4, LBM_GHOST = 8 };
 /* bit 31 of a link-mask word marks a non-fluid cell; bit 30 marks a fluid
- * cell that has at least one INLET or OUTLET link */
+ * cell that has at least one INLET or OUTLET link; bit 29 (with bit 31) marks
+ * a ghost cell */
 #define LBM_MASK_SOLID 0x80000000u
 #define LBM_MASK_SPECIAL 0x40000000u
+#define LBM_MASK_GHOST 0x20000000u
 
 typedef struct lbm_params {
   int32_t stencil;      /* LBM_D2Q9 | LBM_D3Q19 | LBM_D3Q27 */
@@ -341,6 +347,30 @@ lbm_status lbm_eq_vjp(lbm_ctx* ctx, const double* rho0, const double* u0, const 
  * scratch covers), and never calls cudaMalloc or cudaFree. */
 lbm_status lbm_reduce_noalloc(const lbm_params* p, const void* pdf, const uint8_t* flags, int64_t t,
                               double* out, void* stream);
+
+/* Halo exchange of x-slab blocks (Sec. IV-D "Framework Integration": a
+ * block-structured domain partition, with pack and unpack kernels for the
+ * communication between blocks, generated there because for the single-array
+ * patterns which values cross a face depends on the step parity).
+ * A block is a context whose x axis is not periodic, with one ghost layer at
+ * x = 0 and x = nx - 1: flag LBM_GHOST where the neighbouring block's cell is
+ * fluid, its own flag otherwise (NOSLIP outside a non-periodic global
+ * domain); y and z are the global domain's.  After lbm_init_equilibrium /
+ * lbm_set_state and after every step, each block packs what crosses each of
+ * its faces (lbm_halo_pack) and its neighbour across that face unpacks it
+ * (lbm_halo_unpack of the opposite face) before the next step; the blocks
+ * then step like one domain, bit for bit.  Pull and AA patterns only
+ * (LBM_E_UNSUPPORTED otherwise); LBM_E_INVAL for a periodic x axis or
+ * nx < 3.
+ *   face: LBM_FACE_XLOW (x = 0) or LBM_FACE_XHIGH (x = nx - 1);
+ *   buf:  device buffer of lbm_halo_bytes: the crossing directions' values
+ *         ([k][z][y] in the storage type, k over the directions with
+ *         c_x = +1 for XHIGH packs and XLOW unpacks, c_x = -1 otherwise).
+ * Asynchronous on the context's stream. */
+enum { LBM_FACE_XLOW = 0, LBM_FACE_XHIGH = 1 };
+lbm_status lbm_halo_bytes(const lbm_params* p, size_t* bytes);
+lbm_status lbm_halo_pack(lbm_ctx* ctx, int32_t face, void* buf);
+lbm_status lbm_halo_unpack(lbm_ctx* ctx, int32_t face, const void* buf);
 
 /* Block until the context's stream is idle; maps pending CUDA errors
  * (interface plumbing, no method step). */

@@ -10,7 +10,8 @@ Collision"); initialisation sets P = f^eq(rho_0, u_0).  One time step:
 
 Periodic axes wrap; a source outside a non-periodic axis counts as a no-slip
 wall.  Boundaries are per link (Sec. III-C "Boundary Conditions"), decided by
-the flag of the source cell with precedence NOSLIP > INLET > OUTLET:
+the flag of the source cell with precedence NOSLIP > INLET > OUTLET (a flag
+with none of these bits counts as NOSLIP, unless it has the GHOST bit):
 
 - NOSLIP (halfway bounce-back): B_q = P_qbar(x).
 - INLET (velocity bounce-back, UBB listing with c the fluid-to-wall
@@ -23,12 +24,20 @@ the flag of the source cell with precedence NOSLIP > INLET > OUTLET:
   steady state reached from rest.  Which velocity it takes in a transient is
   the reading, which only oracle-vs-GPU agreement checks.
 
+- GHOST (the GHOST bit without NOSLIP, INLET or OUTLET): a ghost cell of a
+  block partition (Sec. IV-D "Framework Integration": the domain is split
+  into blocks that exchange the populations crossing their faces).  It is
+  not updated, like any non-fluid cell, but a link whose source is a ghost
+  cell streams like a fluid link: the ghost holds the populations of the
+  neighbouring block's cell, set from outside.
+
 Output.  ``populations`` returns f(x) (the pre-collision populations the next
 step would collide); ``macroscopic`` returns their moments (Eq. density, with
 the Guo half-force); ``reduce`` returns sum rho, sum rho_0 u and
 (1/2) sum rho |u|^2 over fluid cells; ``link_mask`` sets bit q for every
 boundary link (x, q) of a fluid cell, bit 30 for a fluid cell with an INLET
-or OUTLET link and bit 31 for non-fluid cells.
+or OUTLET link, bit 31 for non-fluid cells and bit 29 (beside bit 31) for
+ghost cells.
 
 Pins: tests/test_oracle_lbm.py (pull streaming against an independent
 np.roll shift, global mass conservation with walls, bounce-back reversing a
@@ -41,18 +50,24 @@ import numpy as np
 from . import collision as co
 from .lattice import CS2
 
-FLUID, NOSLIP, INLET, OUTLET = 0, 1, 2, 4
+FLUID, NOSLIP, INLET, OUTLET, GHOST = 0, 1, 2, 4, 8
 SELF = -1
 CS2F = float(CS2)
 
 
+def is_ghost(flag):
+    flag = np.asarray(flag)
+    return ((flag & (NOSLIP | INLET | OUTLET)) == 0) & ((flag & GHOST) != 0)
+
+
 def link_kind(flag):
-    """Boundary type of a non-fluid source flag, NOSLIP > INLET > OUTLET."""
+    """Type of a link by its source flag: FLUID for a fluid or ghost source,
+    else NOSLIP > INLET > OUTLET (NOSLIP when none of the three bits is set)."""
     flag = np.asarray(flag)
     kind = np.full(flag.shape, NOSLIP, dtype=np.int8)
     kind[((flag & NOSLIP) == 0) & ((flag & INLET) != 0)] = INLET
     kind[((flag & (NOSLIP | INLET)) == 0) & ((flag & OUTLET) != 0)] = OUTLET
-    kind[flag == 0] = FLUID
+    kind[(flag == 0) | is_ghost(flag)] = FLUID
     return kind
 
 
@@ -120,6 +135,7 @@ class Sim:
             special |= self.fluid & ((self.kind[q] == INLET) | (self.kind[q] == OUTLET))
         mask |= special.astype(np.uint64) << np.uint64(30)
         mask |= (~self.fluid).astype(np.uint64) << np.uint64(31)
+        mask |= is_ghost(self.flags).astype(np.uint64) << np.uint64(29)
         return mask.astype(np.uint32)
 
     # -------------------------------------------------------------- stepping

@@ -64,6 +64,9 @@ _SIGS = {
     "lbm_ke_loss_seed": (c_int32, [c_void_p, c_void_p, POINTER(c_int32), c_void_p, c_void_p, c_void_p]),
     "lbm_eq_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_reduce_noalloc": (c_int32, [POINTER(Params), c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "lbm_halo_bytes": (c_int32, [POINTER(Params), POINTER(c_size_t)]),
+    "lbm_halo_pack": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "lbm_halo_unpack": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbm_sync": (c_int32, [c_void_p]),
     "lbm_status_str": (c_char_p, [c_int32]),
     "lbm_debug_fail_host_allocs": (None, [c_int32]),

@@ -834,6 +834,43 @@ lbm_status lbm_eq_vjp(lbm_ctx* c, const double* rho0, const double* u0, const vo
   return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "eq_vjp");
 }
 
+lbm_status lbm_halo_bytes(const lbm_params* p, size_t* bytes) {
+  const char* msg = "";
+  const lbm_status s = validate(p, &msg);
+  if (s != LBM_OK) return s;
+  if (!bytes) return LBM_E_INVAL;
+  const int dirs = p->stencil == LBM_D2Q9 ? 3 : (p->stencil == LBM_D3Q19 ? 5 : 9);
+  *bytes = size_t(dirs) * size_t(p->ny) * size_t(p->nz) * storage_bytes(p->storage);
+  return LBM_OK;
+}
+
+namespace {
+lbm_status halo(lbm_ctx* c, int32_t face, void* buf, int unpack) {
+  if (!c || !buf || (face != LBM_FACE_XLOW && face != LBM_FACE_XHIGH)) return LBM_E_INVAL;
+  if (c->p.pattern != LBM_PULL && c->p.pattern != LBM_AA) {
+    set_err(c, "block halos are built for the pull and AA patterns");
+    return LBM_E_UNSUPPORTED;
+  }
+  if (c->p.periodic[0] || c->p.nx < 3) {
+    set_err(c, "a block needs a non-periodic x axis with ghost layers at x = 0 and nx - 1");
+    return LBM_E_INVAL;
+  }
+  HaloSpec h;
+  h.side = face == LBM_FACE_XHIGH ? 1 : 0;
+  h.mode = c->p.pattern == LBM_PULL ? 0 : ((c->t & 1) ? 1 : 2);
+  h.unpack = unpack;
+  SweepArgs a = make_args(c, nullptr, c->buf[c->cur]);
+  const cudaError_t e = c->ops.halo(a, h, buf, c->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, unpack ? "halo_unpack" : "halo_pack");
+}
+}  // namespace
+
+lbm_status lbm_halo_pack(lbm_ctx* c, int32_t face, void* buf) { return halo(c, face, buf, 0); }
+
+lbm_status lbm_halo_unpack(lbm_ctx* c, int32_t face, const void* buf) {
+  return halo(c, face, const_cast<void*>(buf), 1);
+}
+
 lbm_status lbm_sync(lbm_ctx* c) {
   if (!c) return LBM_E_INVAL;
   cudaError_t e = cudaStreamSynchronize(c->stream);

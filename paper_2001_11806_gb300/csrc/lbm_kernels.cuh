@@ -1243,7 +1243,7 @@ __device__ __forceinline__ uint32_t cell_links(const Geom& g, const uint8_t* fla
     int type = L_NOSLIP;
     if (!solid && flags != nullptr) {
       const uint8_t f = flags[sx + g.nx * (sy + g.ny * sz)];
-      solid = f != 0;
+      solid = !flag_is_fluid_source(f);
       if (solid) type = link_type_of_flag(f);
     }
     if (solid) {
@@ -1264,7 +1264,7 @@ __global__ void k_link_mask(const SweepArgs a, uint32_t* __restrict__ mask, unsi
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < N;
        cell += (long long)gridDim.x * blockDim.x) {
     if (a.flags != nullptr && a.flags[cell] != 0) {
-      mask[cell] = MASK_SOLID;
+      mask[cell] = MASK_SOLID | (flag_is_ghost(a.flags[cell]) ? MASK_GHOST : 0u);
       continue;
     }
     int x, y, z;
@@ -1301,6 +1301,8 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int la
   const long long N = a.g.N;
   uint32_t mask = 0;
   if constexpr (BND) mask = a.mask[cell];
+  // ghost cells receive their populations from the neighbouring block
+  if (mask & MASK_GHOST) return;
   T v[L::Q];  // shifted populations h = P - w
   if (src_kind == 0) {
 #pragma unroll
@@ -1358,6 +1360,78 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int la
     const int qd = b ? p : q;
     const int idx = b ? cell : nb.at(L::cx(q), L::cy(q), L::cz(q));
     pdf_st<S>(a, a.dstq[qd], idx, ST::from_h(v[q], L::w(q)));
+  }
+}
+
+// ------------------------------------------------------------ block halos
+// x-slab blocks with one ghost layer on each x face (local x = 0 and nx - 1,
+// cells flagged LBM_GHOST where the neighbouring block's cell is fluid).  The
+// populations that cross a face between two steps depend on the pattern and
+// the parity (Sec. IV-D: the single-array patterns are why the pack and
+// unpack kernels are generated there).  For the face x = nx - 1 (side 1) and
+// the directions q with c_x = +1 that cross it:
+//   pack (what this block sends):
+//     pull:            P_q at the last interior layer (x = nx - 2), slot q
+//     AA, odd t:       the even step left P_q(x) in slot qbar of x = nx - 2
+//     AA, even t > 0 or after initialisation: the odd step (or the push
+//                      initialisation) wrote P_q of the last layer into slot
+//                      q of the ghost layer x = nx - 1
+//   unpack (what the neighbour across the face x = 0 stores):
+//     pull: slot q of its ghost layer x = 0; AA odd t: slot qbar of x = 0;
+//     AA even t: slot q of its first interior layer x = 1.
+// The face x = 0 (side 0) mirrors this with the directions c_x = -1 and the
+// layers 1, 0 (pack) and nx - 1, nx - 2 (unpack).  Buffer layout
+// [k][z][y] for the k-th crossing direction, in the storage type.  Values
+// for non-fluid positions travel too; they land in slots no sweep reads.
+struct HaloSpec {
+  int side;    // 0: face x = 0, 1: face x = nx - 1
+  int mode;    // 0: pull, 1: AA with odd t, 2: AA with even t
+  int unpack;  // 0: pack into buf, 1: unpack from buf
+};
+
+template <class L>
+__host__ __device__ constexpr int halo_dirs() {
+  int n = 0;
+  for (int q = 0; q < L::Q; ++q) n += L::cx(q) == 1 ? 1 : 0;
+  return n;
+}
+
+template <class L>
+__device__ __forceinline__ int halo_dir(int k, int sign) {
+  int n = 0;
+  for (int q = 0; q < L::Q; ++q)
+    if (L::cx(q) == sign) {
+      if (n == k) return q;
+      ++n;
+    }
+  return 0;
+}
+
+template <class L, class ST>
+__global__ void k_halo(const SweepArgs a, HaloSpec h, typename ST::S* buf) {
+  using S = typename ST::S;
+  const long long plane = (long long)a.g.ny * a.g.nz;
+  const long long total = plane * halo_dirs<L>();
+  const int nx = a.g.nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = int(i / plane);
+    const long long yz = i - k * plane;  // y + ny z
+    // directions that cross the face outward (pack) or inward (unpack)
+    const int sign = (h.side == 1) != (h.unpack != 0) ? 1 : -1;
+    const int q = halo_dir<L>(k, sign);
+    int x, slot;
+    if (h.unpack == 0) {
+      if (h.mode == 2) x = h.side == 1 ? nx - 1 : 0;
+      else x = h.side == 1 ? nx - 2 : 1;
+    } else {
+      if (h.mode == 2) x = h.side == 1 ? nx - 2 : 1;
+      else x = h.side == 1 ? nx - 1 : 0;
+    }
+    slot = h.mode == 1 ? opp(q) : q;
+    S* p = static_cast<S*>(a.dst) + (long long)slot * a.g.N + x + (long long)nx * yz;
+    if (h.unpack == 0) buf[i] = *p;
+    else *p = buf[i];
   }
 }
 

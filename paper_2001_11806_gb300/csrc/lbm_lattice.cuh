@@ -110,9 +110,16 @@ struct StF32S {
 };
 
 // Flag bits (uint8 per cell) and link-mask bits, as in include/lbm.h.
-enum : uint8_t { F_NOSLIP = 1, F_INLET = 2, F_OUTLET = 4 };
+enum : uint8_t { F_NOSLIP = 1, F_INLET = 2, F_OUTLET = 4, F_GHOST = 8 };
 constexpr uint32_t MASK_SOLID = 0x80000000u;
 constexpr uint32_t MASK_SPECIAL = 0x40000000u;  // the cell has an inlet or outlet link
+constexpr uint32_t MASK_GHOST = 0x20000000u;    // a ghost cell (also MASK_SOLID: not swept)
+
+// A ghost cell (GHOST bit without NOSLIP, INLET or OUTLET) holds populations
+// of a neighbouring block: it is not swept, but links from it stream like
+// fluid links.
+__host__ __device__ inline bool flag_is_ghost(uint8_t f) { return (f & 7) == 0 && (f & F_GHOST) != 0; }
+__host__ __device__ inline bool flag_is_fluid_source(uint8_t f) { return f == 0 || flag_is_ghost(f); }
 enum LinkType : int { L_NOSLIP = 1, L_INLET = 2, L_OUTLET = 4 };
 
 __host__ __device__ inline int link_type_of_flag(uint8_t f) {

@@ -90,6 +90,13 @@ struct Ops {
   }
 };
 
+template <class L, class ST>
+cudaError_t launch_halo(const SweepArgs& a, HaloSpec h, void* buf, cudaStream_t s) {
+  const long long n = (long long)a.g.ny * a.g.nz * halo_dirs<L>();
+  k_halo<L, ST><<<grid_stride_blocks(n, 256), 256, 0, s>>>(a, h, static_cast<typename ST::S*>(buf));
+  return cudaGetLastError();
+}
+
 template <class L>
 cudaError_t launch_link_mask(const SweepArgs& a, uint32_t* mask, unsigned* types, cudaStream_t s) {
   k_link_mask<L><<<grid_stride_blocks(a.g.N, 256), 256, 0, s>>>(a, mask, types);
@@ -131,6 +138,7 @@ struct OpsTable {
   cudaError_t (*list_count)(const SweepArgs&, int, int*, cudaStream_t);
   cudaError_t (*list_scatter)(const SweepArgs&, int, const int*, uint2*, cudaStream_t);
   cudaError_t (*boundary_pull)(const SweepArgs&, void*, cudaStream_t);
+  cudaError_t (*halo)(const SweepArgs&, HaloSpec, void*, cudaStream_t);
 };
 
 template <class L, class ST>
@@ -138,7 +146,8 @@ OpsTable make_table() {
   return OpsTable{&Ops<L, ST>::sweep,          &Ops<L, ST>::populations, &Ops<L, ST>::macroscopic,
                   &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>,
                   &Ops<L, ST>::adjoint,        &Ops<L, ST>::ke_seed,     &Ops<L, ST>::eq_vjp,
-                  &launch_list_count<L>,       &launch_list_scatter<L>,  &launch_boundary_pull<L, ST>};
+                  &launch_list_count<L>,       &launch_list_scatter<L>,  &launch_boundary_pull<L, ST>,
+                  &launch_halo<L, ST>};
 }
 
 #define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();

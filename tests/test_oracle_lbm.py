@@ -143,10 +143,12 @@ def test_link_mask_brute_force():
 
 
 def test_link_kind_of_every_flag_value():
-    # the documented rule for a uint8 flag: 0 is fluid; otherwise NOSLIP if
-    # bit 0 is set or no known bit is set, else INLET if bit 1, else OUTLET
+    # the documented rule for a uint8 flag: 0 is fluid; the GHOST bit (8)
+    # without bits 0-2 is a ghost source, which streams like fluid; otherwise
+    # NOSLIP if bit 0 is set or no known bit is set, else INLET if bit 1,
+    # else OUTLET
     for v in range(256):
-        if v == 0:
+        if v == 0 or (v & 8 and not v & 7):
             want = lbm.FLUID
         elif v & 1 or not v & 6:
             want = lbm.NOSLIP
@@ -175,3 +177,69 @@ def test_ubb_at_rest_is_bounce_back(name):
         s.step(3)
         out.append(s.populations())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("periodic_x", [True, False])
+def test_ghost_blocks_reproduce_the_undivided_domain(name, periodic_x):
+    """A block partition in x (Sec. IV-D, the framework's block-structured
+    domain): each block carries one ghost layer per x face, flagged GHOST
+    where the neighbouring block's cell is fluid, and after every step the
+    ghost cells take the post-collision populations of the cells they stand
+    for.  Then every block's interior equals the undivided domain exactly;
+    a plausible mistake (ghosts treated as walls, a ghost not refreshed, a
+    block boundary shifted by one) breaks it."""
+    lat = lattice.get(name)
+    shp = _shape(lat, (12, 5, 4))
+    nx = shp[0]
+    flags = np.zeros(shp[::-1], np.uint8)
+    r = inputs.uniform(17, flags.size).reshape(flags.shape)
+    flags[r < 0.12] = lbm.NOSLIP
+    if not periodic_x:
+        flags[..., 0] = lbm.INLET
+        flags[..., -1] = lbm.OUTLET
+    per = (periodic_x, True, True)
+    m = co.Method(lat, "trt", [1.6, 0.9])
+    whole = lbm.Sim(m, shp, periodic=per, flags=flags, u_wall=(0.03, 0.0, 0.0))
+    P = inputs.random_pdfs(lat.w, shp[::-1], seed=18)
+    whole.P = P.copy()
+    cuts = [0, 5, nx]
+    blocks = []
+    for b in range(2):
+        x0, x1 = cuts[b], cuts[b + 1]
+        xs = [(x - 1) for x in range(x0, x1 + 2)]  # global x of local 0 .. nb + 1
+        fl = np.zeros(shp[::-1][:-1] + (len(xs),), np.uint8)
+        for i, gx in enumerate(xs):
+            inside = 0 <= gx < nx
+            g = gx % nx
+            if 1 <= i <= x1 - x0:
+                fl[..., i] = flags[..., g]
+            elif not inside and not periodic_x:
+                fl[..., i] = lbm.NOSLIP
+            else:
+                fl[..., i] = np.where(flags[..., g] == 0, lbm.GHOST, flags[..., g])
+        s = lbm.Sim(m, (len(xs), shp[1], shp[2]), periodic=(False, True, True), flags=fl, u_wall=(0.03, 0.0, 0.0))
+        s.P = P[..., [x % nx for x in xs]].copy()
+        blocks.append((s, xs, fl))
+
+    def refresh():
+        for s, xs, fl in blocks:
+            for i in (0, len(xs) - 1):
+                gx = xs[i]
+                owner = [o for o in blocks if o[1][1] <= gx % nx <= o[1][-2]]
+                if (0 <= gx < nx or periodic_x) and owner:
+                    o, oxs, _ = owner[0]
+                    s.P[..., i] = o.P[..., oxs.index(gx % nx)]
+    refresh()
+    for _ in range(4):
+        whole.step(1)
+        for s, _, _ in blocks:
+            s.step(1)
+        refresh()
+    for s, xs, fl in blocks:
+        inner = slice(1, len(xs) - 1)
+        assert np.array_equal(s.populations()[..., inner], whole.populations()[..., xs[1]:xs[-2] + 1])
+    # the ghost bit in the mask
+    s, xs, fl = blocks[0]
+    mk = s.link_mask()
+    assert np.all(((mk >> 29) & 1).astype(bool) == lbm.is_ghost(fl))

@@ -329,8 +329,24 @@ def run_variants(device, peak, only=None, steps_override=None, warmup=10):
                                                   shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
         ("D3Q19 TRT FP16-shifted 256^3 AA", dict(stencil="D3Q19", collision="trt", storage="f16s", pattern="aa",
                                                  shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
+        ("D3Q19 TRT FP16-shifted 256^3 two-grid pull", dict(stencil="D3Q19", collision="trt", storage="f16s",
+                                                            pattern="pull", shape=(256,) * 3, omega=[OMEGA_E],
+                                                            trt_magic=MAGIC), "tgv", 300),
+        ("D3Q19 TRT FP16-shifted 256^3 esoteric twist", dict(stencil="D3Q19", collision="trt", storage="f16s",
+                                                             pattern="eso", shape=(256,) * 3, omega=[OMEGA_E],
+                                                             trt_magic=MAGIC), "tgv", 300),
         ("D3Q19 TRT FP32 256^3 esoteric twist", dict(stencil="D3Q19", collision="trt", storage="f32", pattern="eso",
                                                      shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 300),
+        ("D3Q19 MRT FP32 256^3 AA, one higher-order rate", dict(stencil="D3Q19", collision="mrt", storage="f32",
+                                                                pattern="aa", shape=(256,) * 3,
+                                                                omega=[1.7, 1.0, 1.0, 1.0]), "tgv", 200),
+        ("D3Q19 MRT FP32 256^3 AA, four rates (moment matrix)", dict(stencil="D3Q19", collision="mrt",
+                                                                     storage="f32", pattern="aa", shape=(256,) * 3,
+                                                                     omega=[1.7, 1.1, 0.9, 1.3]), "tgv", 200),
+        ("D3Q27 TRT FP32 256^3 AA", dict(stencil="D3Q27", collision="trt", storage="f32", pattern="aa",
+                                         shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 200),
+        ("D3Q19 TRT FP64 256^3 AA", dict(stencil="D3Q19", collision="trt", storage="f64", pattern="aa",
+                                         shape=(256,) * 3, omega=[OMEGA_E], trt_magic=MAGIC), "tgv", 50),
         ("D3Q19 SRT + Smagorinsky (C_S 0.17) FP32 256^3 AA",
          dict(stencil="D3Q19", collision="srt", storage="f32", pattern="aa", shape=(256,) * 3, omega=[1.95],
               smagorinsky_cs=0.17), "tgv", 300),

@@ -1,7 +1,8 @@
 """Flag values with several bits set, or with bits the library does not name,
 on the GPU: the link mask stays bit-exact with the oracle and the populations
 match it (a link takes NOSLIP if its source flag has bit 0 or no known bit,
-else INLET if bit 1, else OUTLET).  The same channel with the flags reduced
+else INLET if bit 1, else OUTLET; the GHOST bit 8 counts only without the
+other three).  The same channel with the flags reduced
 to their single types gives bitwise the same GPU result."""
 import numpy as np
 import pytest
@@ -31,16 +32,17 @@ def _flags(shape, seed=9):
 
 
 def _mixed(fl, seed=10):
-    """Same link types, other bit patterns: NOSLIP -> 1|2, 1|4, 8 or 255;
-    INLET -> 2|4; OUTLET -> 4|16."""
+    """Same link types, other bit patterns: NOSLIP -> 1|2, 1|4, 16 or 255;
+    INLET -> 2|4 or 2|8; OUTLET -> 4|16."""
     r = inputs.uniform(seed, fl.size).reshape(fl.shape)
     out = fl.copy()
     ns = fl == olbm.NOSLIP
     out[ns & (r < 0.25)] = 3
     out[ns & (r >= 0.25) & (r < 0.5)] = 5
-    out[ns & (r >= 0.5) & (r < 0.75)] = 8
+    out[ns & (r >= 0.5) & (r < 0.75)] = 16
     out[ns & (r >= 0.75)] = 255
     out[(fl == olbm.INLET) & (r < 0.5)] = 6
+    out[(fl == olbm.INLET) & (r >= 0.5) & (r < 0.75)] = 10
     out[(fl == olbm.OUTLET) & (r < 0.5)] = 20
     return out
 

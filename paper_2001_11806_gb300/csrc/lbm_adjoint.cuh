@@ -117,14 +117,41 @@ __device__ __forceinline__ void collide_vjp(T drho, const T (&jh)[3], const T (&
   const bool comp = p.incompressible == 0;
   const T rho = T(1) + drho;
   const T inv0 = comp ? T(1) / rho : T(1);
-  if constexpr (OP == OP_MRT) relax_transpose<L, T, OP>(lam, nu, p);
   T n0 = T(0), n1[3] = {T(0), T(0), T(0)}, k0 = T(0), k1[3] = {T(0), T(0), T(0)};
   Sym3<T> N2, K2;
+  if constexpr (OP == OP_MRT) {
+    relax_transpose<L, T, OP>(lam, nu, p);
 #pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    const T nq = OP == OP_MRT ? nu[q] : nu_pair<L, T, OP>(lam, q, p);
-    wmoments<L, T>(q, nq, n0, n1, N2);
-    if (force) wmoments<L, T>(q, lam[q] - T(0.5) * nq, k0, k1, K2);
+    for (int q = 0; q < L::Q; ++q) {
+      wmoments<L, T>(q, nu[q], n0, n1, N2);
+      if (force) wmoments<L, T>(q, lam[q] - T(0.5) * nu[q], k0, k1, K2);
+    }
+  } else {
+    // SRT/TRT: nu = R^T lambda scales the even pair parts by omega_e and the
+    // odd ones by omega_o, and the weights are even in c, so the weighted
+    // moments of nu (and of kappa = lambda - nu/2) are those of lambda
+    // scaled: orders 0 and 2 by omega_e, order 1 by omega_o.  One pass over
+    // lambda instead of two over nu and kappa.
+    T l0 = T(0), l1[3] = {T(0), T(0), T(0)};
+    Sym3<T> L2;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) wmoments<L, T>(q, lam[q], l0, l1, L2);
+    const T oe = rate<T>(p, 0);
+    const T oo = OP == OP_SRT ? oe : rate<T>(p, 1);
+    auto scale = [](const Sym3<T>& m, T f) {
+      Sym3<T> r;
+      r.xx = f * m.xx; r.yy = f * m.yy; r.zz = f * m.zz; r.xy = f * m.xy; r.xz = f * m.xz; r.yz = f * m.yz;
+      return r;
+    };
+    n0 = oe * l0;
+    for (int d = 0; d < 3; ++d) n1[d] = oo * l1[d];
+    N2 = scale(L2, oe);
+    if (force) {
+      const T he = T(1) - T(0.5) * oe, ho = T(1) - T(0.5) * oo;
+      k0 = he * l0;
+      for (int d = 0; d < 3; ++d) k1[d] = ho * l1[d];
+      K2 = scale(L2, he);
+    }
   }
   T N2J[3];
   sym_mul(N2, J, N2J);

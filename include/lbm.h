@@ -366,6 +366,8 @@ lbm_status lbm_reduce_noalloc(const lbm_params* p, const void* pdf, const uint8_
  *   buf:  device buffer of lbm_halo_bytes: the crossing directions' values
  *         ([k][z][y] in the storage type, k over the directions with
  *         c_x = +1 for XHIGH packs and XLOW unpacks, c_x = -1 otherwise).
+ *         An unpack leaves the receiver's own boundary values in place (links
+ *         whose source across the face is not fluid).
  * Asynchronous on the context's stream. */
 enum { LBM_FACE_XLOW = 0, LBM_FACE_XHIGH = 1 };
 lbm_status lbm_halo_bytes(const lbm_params* p, size_t* bytes);

@@ -1378,7 +1378,9 @@ __global__ void __launch_bounds__(kBlockX) k_init_push(const SweepArgs a, int la
 //                      q of the ghost layer x = nx - 1
 //   unpack (what the neighbour across the face x = 0 stores):
 //     pull: slot q of its ghost layer x = 0; AA odd t: slot qbar of x = 0;
-//     AA even t: slot q of its first interior layer x = 1.
+//     AA even t: slot q of its first interior layer x = 1, except where that
+//     slot holds the receiver's own boundary value (the link (x, q) comes
+//     from a non-fluid cell across the face) or the cell is not fluid.
 // The face x = 0 (side 0) mirrors this with the directions c_x = -1 and the
 // layers 1, 0 (pack) and nx - 1, nx - 2 (unpack).  Buffer layout
 // [k][z][y] for the k-th crossing direction, in the storage type.  Values
@@ -1429,9 +1431,21 @@ __global__ void k_halo(const SweepArgs a, HaloSpec h, typename ST::S* buf) {
       else x = h.side == 1 ? nx - 1 : 0;
     }
     slot = h.mode == 1 ? opp(q) : q;
-    S* p = static_cast<S*>(a.dst) + (long long)slot * a.g.N + x + (long long)nx * yz;
-    if (h.unpack == 0) buf[i] = *p;
-    else *p = buf[i];
+    const long long cell = x + (long long)nx * yz;
+    S* p = static_cast<S*>(a.dst) + (long long)slot * a.g.N + cell;
+    if (h.unpack == 0) {
+      buf[i] = *p;
+    } else {
+      // into an interior cell (AA, even t): not where the receiver keeps a
+      // boundary value of its own (a non-fluid cell, or a link whose source
+      // across the face is non-fluid, whose slot the receiver's odd step
+      // filled with B_q)
+      if (h.mode == 2 && a.mask != nullptr) {
+        const uint32_t m = a.mask[cell];
+        if ((m & MASK_SOLID) || ((m >> q) & 1u)) continue;
+      }
+      *p = buf[i];
+    }
   }
 }
 

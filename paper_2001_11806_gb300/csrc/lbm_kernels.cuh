@@ -673,27 +673,6 @@ __device__ __forceinline__ void store_special_links(const SweepArgs& a, const ty
   }
 }
 
-// The same values put into the post-collision populations before the common
-// stores: for a boundary link (x, p = qbar) direction q is stored into the
-// link's own slot, so v[q] takes B_p(P(x)) (bitwise what the re-store gives).
-template <class L, class T, bool DH>
-__device__ __forceinline__ void fix_special_links(const SweepArgs& a, T (&v)[L::Q], int cs, uint32_t ms) {
-  int x, y, z;
-  cell_coords(a.g, cs, x, y, z);
-  const OutletP op = outlet_params(a.cp);
-  T up[3];
-  post_velocity<L, T, DH>(v, op, up);
-#pragma unroll
-  for (int q = 1; q < L::Q; ++q) {
-    const int p = opp(q);
-    if ((ms >> p) & 1u) {
-      const int t = LBM_LINK_TYPE(a, x + L::cx(q), y + L::cy(q), z + L::cz(q));
-      if (t == L_INLET) v[q] += ubb_term<L, T>(p, a.cp);
-      else if (t == L_OUTLET) v[q] = outlet_value<L, T, DH>(p, up, op);
-    }
-  }
-}
-
 // One list entry (cell, link-mask word) at list position i.
 template <class L, class ST, int OP, int KIND, bool WRAP>
 __device__ __forceinline__ void sweep_list(const SweepArgs& a, const uint2 entry, const int i) {
@@ -898,8 +877,7 @@ __global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArg
 // collided, and in the AA odd step stores nothing (its stores would land in
 // its neighbours' slots); in the pull and the AA even step its own slots
 // take the pair's store, which no sweep reads.  Inlet and outlet links (AA)
-// take their values in FP32 before the packing (pull pairs have none: those
-// cells are in the second launch).
+// are stored again afterwards from the stored binary16 values.
 template <class L, int OP, int KIND>
 __global__ void __launch_bounds__(kBlockX) k_sweep_pairs_h2(const SweepArgs a) {
   using ST = StF16S;
@@ -935,9 +913,6 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_pairs_h2(const SweepArgs a) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
     collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
-    if constexpr (KIND != K_PULL) {
-      if (e.y & MASK_SPECIAL) fix_special_links<L, T, true>(a, v, int(c0), e.y);
-    }
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__float2half_rn(v[q]), __high2half(P[q]));
   }
@@ -946,9 +921,6 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_pairs_h2(const SweepArgs a) {
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
     collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
-    if constexpr (KIND != K_PULL) {
-      if (e.z & MASK_SPECIAL) fix_special_links<L, T, true>(a, v, int(c0 + 1u), e.z);
-    }
 #pragma unroll
     for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__low2half(P[q]), __float2half_rn(v[q]));
   }
@@ -978,6 +950,20 @@ __global__ void __launch_bounds__(kBlockX) k_sweep_pairs_h2(const SweepArgs a) {
         if (g0) pdf_st<S>(a, base, i0, __low2half(P[q]));
         if (g1) pdf_st<S>(a, base, i1, __high2half(P[q]));
       }
+    }
+  }
+  if constexpr (KIND != K_PULL) {
+    if (g0 && (es.y & MASK_SPECIAL)) {
+      T v[L::Q];
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
+      store_special_links<L, ST, true, KIND>(a, v, int(s0), es.y);
+    }
+    if (g1 && (es.z & MASK_SPECIAL)) {
+      T v[L::Q];
+#pragma unroll
+      for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
+      store_special_links<L, ST, true, KIND>(a, v, int(s0 + 1u), es.z);
     }
   }
 }

@@ -69,9 +69,6 @@ struct lbm_ctx {
   bool has_mask = false;
   uint2* list = nullptr;  // fluid cells of a masked domain with their mask words (SweepArgs::list)
   int n_main = 0, n_wrap = 0;
-  uint4* pairs = nullptr;  // 16-bit storage: aligned cell pairs of the main launch (SweepArgs::pairs)
-  int n_pairs = 0;
-  bool pair_mode = false;
   unsigned link_types = 0;  // OR of the boundary-link types present (L_INLET, L_OUTLET)
   cudaStream_t stream = nullptr;
   int64_t t = 0;
@@ -101,7 +98,7 @@ constexpr int kGraphSteps = 32;
 constexpr long long kGraphMaxCells = 1 << 20;
 
 struct Layout {
-  size_t mask_off, mask_bytes, list_off, count_off, part_off, adj_off, pair_off, res_off, total;
+  size_t mask_off, mask_bytes, list_off, count_off, part_off, adj_off, res_off, total;
   int nblk;  // chunks of the fluid-list builder
 };
 
@@ -120,8 +117,7 @@ bool needs_mask(const lbm_params& p, bool has_flags) {
 
 // aux = [link mask: 4 N bytes][fluid-cell list: 8 N bytes][list-builder
 // counts: 2 x 4 x nblk bytes][reduction partials][adjoint force rows: 3
-// doubles per sweep block][cell pairs, D3Q19 16-bit storage: 16 B per pair]
-// [reduction result]; the mask
+// doubles per sweep block][reduction result]; the mask
 // and list regions are always reserved so that the size does not depend on
 // the flags.
 Layout layout_for(const lbm_params& p, long long N) {
@@ -137,11 +133,7 @@ Layout layout_for(const lbm_params& p, long long N) {
   g.ny = p.ny;
   g.nz = p.nz;
   l.adj_off = l.part_off + align256(size_t(kRedMaxBlocks) * 5 * sizeof(double));
-  l.pair_off = l.adj_off + align256(size_t(adjoint_rows(g)) * 3 * sizeof(double));
-  // D3Q19 with 16-bit storage: room for the cell-pair list (16 B per pair)
-  const size_t pair_bytes =
-      (p.stencil == LBM_D3Q19 && p.storage == LBM_F16S) ? align256(size_t((N + 1) / 2) * sizeof(uint4)) : 0;
-  l.res_off = l.pair_off + pair_bytes;
+  l.res_off = l.adj_off + align256(size_t(adjoint_rows(g)) * 3 * sizeof(double));
   l.total = l.res_off + 256;
   return l;
 }
@@ -281,47 +273,6 @@ lbm_status build_list(lbm_ctx* c, const SweepArgs& a, const Layout& lay) {
   return LBM_OK;
 }
 
-// Cell-pair list of the 16-bit pair sweep (see k_sweep_pairs_h2), after the
-// cell list was built with pair-aware categories: per-chunk counts, host
-// scan, ordered scatter, as for the cell list.
-lbm_status build_pairs(lbm_ctx* c, const SweepArgs& a, const Layout& lay) {
-  int* counts = reinterpret_cast<int*>(static_cast<char*>(c->aux) + lay.count_off);
-  const long long npairs = c->N / 2;
-  const int nblk = int((npairs + kListChunk - 1) / kListChunk);  // <= lay.nblk
-  if (nblk == 0) return LBM_OK;
-  int* h = injected_alloc_failure() ? nullptr : static_cast<int*>(std::malloc(size_t(nblk) * sizeof(int)));
-  if (!h) {
-    set_err(c, "host allocation of the pair offsets failed");
-    return LBM_E_NOMEM;
-  }
-  struct Free {
-    int* p;
-    ~Free() { std::free(p); }
-  } guard{h};
-  cudaError_t e = c->ops.pair_count(a, nblk, counts, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts, size_t(nblk) * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) {
-    set_err(c, "pair count: ", cudaGetErrorString(e));
-    return LBM_E_CUDA;
-  }
-  long long run = 0;
-  for (int b = 0; b < nblk; ++b) {
-    const int k = h[b];
-    h[b] = int(run);
-    run += k;
-  }
-  c->n_pairs = int(run);
-  e = cudaMemcpyAsync(counts, h, size_t(nblk) * sizeof(int), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = c->ops.pair_scatter(a, nblk, counts, c->pairs, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) {
-    set_err(c, "pair scatter: ", cudaGetErrorString(e));
-    return LBM_E_CUDA;
-  }
-  return LBM_OK;
-}
-
 lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
   set_err(c, where, ": ", cudaGetErrorString(e));
   return LBM_E_CUDA;
@@ -371,9 +322,6 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
   a.boundary_mode = c->p.boundary_mode;
   a.special_wrap = (c->p.pattern == LBM_PULL && c->p.boundary_mode == LBM_BOUNDARY_IN_SWEEP) ? 1 : 0;
   a.list_ahead = 0;
-  a.pairs = c->n_pairs > 0 || c->pair_mode ? c->pairs : nullptr;
-  a.n_pairs = c->n_pairs;
-  a.pair_mode = c->pair_mode ? 1 : 0;
   a.pdf_bytes = c->pdf_bytes;
   a.bounds_flag = bounds_word(c);
   for (int q = 0; q < 27; ++q) {
@@ -637,15 +585,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
       return LBM_E_UNSUPPORTED;
     }
     c->list = reinterpret_cast<uint2*>(static_cast<char*>(aux) + lay.list_off);
-    // 16-bit D3Q19 under SRT/TRT/one-rate MRT, pull or AA, even nx: the main
-    // launch runs over aligned cell pairs
-    const bool light = c->kernel_op == OP_SRT || c->kernel_op == OP_TRT || c->kernel_op == OP_MRT3;
-    c->pair_mode = p->stencil == LBM_D3Q19 && p->storage == LBM_F16S && light &&
-                   (p->pattern == LBM_PULL || p->pattern == LBM_AA) && (p->nx % 2) == 0;
-    if (c->pair_mode) c->pairs = reinterpret_cast<uint4*>(static_cast<char*>(aux) + lay.pair_off);
-    SweepArgs ab = make_args(c, nullptr, nullptr);
-    lbm_status ls = build_list(c, ab, lay);
-    if (ls == LBM_OK && c->pair_mode) ls = build_pairs(c, ab, lay);
+    const lbm_status ls = build_list(c, a, lay);
     if (ls != LBM_OK) {
       delete c;
       return ls;

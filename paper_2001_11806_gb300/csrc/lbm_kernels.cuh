@@ -86,13 +86,6 @@ struct SweepArgs {
   int n_main, n_wrap;
   int boundary_mode;  // LBM_BOUNDARY_SEPARATE: the sweep streams every link as fluid
   int special_wrap;   // list builder: cells with inlet/outlet links go to the second launch
-  // 16-bit storage: the main launch over aligned cell pairs (2k, 2k + 1) as
-  // (cell 2k, mask word of 2k, mask word of 2k + 1, 0), a non-fluid cell's
-  // word being MASK_SOLID; pair_mode makes the list builder send a cell to
-  // the second launch when its partner goes there
-  const uint4* pairs;
-  int n_pairs;
-  int pair_mode;
   int list_ahead;     // main list launch: distance, in entries, of the L2 prefetch of entries
   // masked sweeps: element offsets, relative to the cell and to the stream of
   // the lower slot of the pair (q, qbar), of the population direction q
@@ -479,29 +472,15 @@ __device__ __forceinline__ void cell_coords(const Geom& g, long long cell, int& 
 // inlet or outlet link: the pull fixes those values up before the collision,
 // which the main launch does not carry
 template <class L>
-__device__ __forceinline__ bool list_wraps(const SweepArgs& a, long long cell, uint32_t m) {
-  if ((m & MASK_SPECIAL) && a.special_wrap) return true;
+__device__ __forceinline__ int list_category(const SweepArgs& a, long long cell) {
+  const uint32_t m = a.mask[cell];
+  if (m & MASK_SOLID) return 0;
+  if ((m & MASK_SPECIAL) && a.special_wrap) return 2;
   int x, y, z;
   cell_coords(a.g, cell, x, y, z);
   bool wrap = (a.g.per[0] && (x == 0 || x == a.g.nx - 1)) || (a.g.per[1] && (y == 0 || y == a.g.ny - 1));
   if constexpr (L::D == 3) wrap = wrap || (a.g.per[2] && (z == 0 || z == a.g.nz - 1));
-  return wrap;
-}
-
-template <class L>
-__device__ __forceinline__ int list_category(const SweepArgs& a, long long cell) {
-  const uint32_t m = a.mask[cell];
-  if (m & MASK_SOLID) return 0;
-  if (list_wraps<L>(a, cell, m)) return 2;
-  if (a.pair_mode) {
-    // the pair sweep takes both cells of a pair or neither
-    const long long partner = cell ^ 1;
-    if (partner < a.g.N) {
-      const uint32_t mp = a.mask[partner];
-      if (!(mp & MASK_SOLID) && list_wraps<L>(a, partner, mp)) return 2;
-    }
-  }
-  return 1;
+  return wrap ? 2 : 1;
 }
 
 constexpr int kListThreads = 256;
@@ -567,62 +546,6 @@ __global__ void __launch_bounds__(kListThreads) k_list_scatter(const SweepArgs a
     if (cat == 2) list[base2 + pre2 + __popc(m2 & below)] = make_uint2(unsigned(cell), word);
     base1 += tot1;
     base2 += tot2;
-    __syncthreads();
-  }
-}
-
-// Pair lists (16-bit storage, even nx): pair k = cells (2k, 2k + 1) goes to
-// the pair sweep when one of its cells is a main-list cell (then neither is
-// in the second launch).  counts[b]: such pairs in chunk b.
-template <class L>
-__device__ __forceinline__ bool pair_in_list(const SweepArgs& a, long long k) {
-  const long long c0 = 2 * k;
-  return list_category<L>(a, c0) == 1 || (c0 + 1 < a.g.N && list_category<L>(a, c0 + 1) == 1);
-}
-
-template <class L>
-__global__ void __launch_bounds__(kListThreads) k_pair_count(const SweepArgs a, int nblk, int* __restrict__ counts) {
-  __shared__ int sm;
-  if (threadIdx.x == 0) sm = 0;
-  __syncthreads();
-  const long long npairs = a.g.N / 2;
-  int c = 0;
-  for (int k = 0; k < 4; ++k) {
-    const long long pk = (long long)blockIdx.x * kListChunk + k * kListThreads + threadIdx.x;
-    if (pk < npairs) c += pair_in_list<L>(a, pk);
-  }
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&sm, c);
-  __syncthreads();
-  if (threadIdx.x == 0) counts[blockIdx.x] = sm;
-}
-
-template <class L>
-__global__ void __launch_bounds__(kListThreads) k_pair_scatter(const SweepArgs a, int nblk,
-                                                                const int* __restrict__ offsets, uint4* __restrict__ pairs) {
-  __shared__ int warp_tot[kListThreads / 32];
-  int base = offsets[blockIdx.x];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long npairs = a.g.N / 2;
-  for (int k = 0; k < 4; ++k) {
-    const long long pk = (long long)blockIdx.x * kListChunk + k * kListThreads + threadIdx.x;
-    const bool in = pk < npairs && pair_in_list<L>(a, pk);
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if (lane == 0) warp_tot[wid] = __popc(m);
-    __syncthreads();
-    int pre = 0, tot = 0;
-    for (int w = 0; w < kListThreads / 32; ++w) {
-      if (w < wid) pre += warp_tot[w];
-      tot += warp_tot[w];
-    }
-    if (in) {
-      const long long c0 = 2 * pk;
-      const uint32_t m0 = a.mask[c0], m1 = a.mask[c0 + 1];
-      const uint32_t w0 = (m0 & MASK_SOLID) ? MASK_SOLID : (a.boundary_mode ? 0u : m0);
-      const uint32_t w1 = (m1 & MASK_SOLID) ? MASK_SOLID : (a.boundary_mode ? 0u : m1);
-      pairs[base + pre + __popc(m & ((1u << lane) - 1u))] = make_uint4(unsigned(c0), w0, w1, 0u);
-    }
-    base += tot;
     __syncthreads();
   }
 }
@@ -864,108 +787,6 @@ constexpr bool list_capped() {
 template <class L, class ST, int OP, int KIND>
 __global__ void __maxnreg__(LBM_LIST_MAXNREG) k_sweep_list_capped(const SweepArgs a) {
   sweep_list_main<L, ST, OP, KIND>(a);
-}
-
-// Main launch of masked 16-bit domains over aligned cell pairs (2k, 2k + 1),
-// for the two-grid pull and AA with an even nx (then a pair never straddles
-// two rows and every stream starts on a 4-byte boundary).  As in k_sweep_h2
-// the two cells' populations of a direction sit packed in one __half2
-// register and are collided one cell at a time.  A direction with c_x = 0
-// whose link is of the same kind for both cells moves both values with one
-// aligned 4-byte access; the others take two 2-byte accesses.  A non-fluid
-// cell of a pair reads its own slots (always inside the box), is not
-// collided, and in the AA odd step stores nothing (its stores would land in
-// its neighbours' slots); in the pull and the AA even step its own slots
-// take the pair's store, which no sweep reads.  Inlet and outlet links (AA)
-// are stored again afterwards from the stored binary16 values.
-template <class L, int OP, int KIND>
-__global__ void __launch_bounds__(kBlockX) k_sweep_pairs_h2(const SweepArgs a) {
-  using ST = StF16S;
-  using T = float;
-  using S = __half;
-  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-  {
-    const unsigned ahead = i + unsigned(a.list_ahead);  // n_pairs < 2^30, list_ahead < 2^30: no wrap
-    if ((threadIdx.x & 7) == 0 && ahead < unsigned(a.n_pairs)) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.pairs + ahead));
-  }
-  if (i >= unsigned(a.n_pairs)) return;
-  const uint4 e = a.pairs[i];
-  const unsigned c0 = e.x;
-  const bool f0 = !(e.y & MASK_SOLID), f1 = !(e.z & MASK_SOLID);
-  __half2 P[L::Q];
-#pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    if constexpr (KIND == K_AA_EVEN) {
-      P[q] = pdf_ld<__half2>(a, reinterpret_cast<const __half*>(a.srcq[q]) + c0, 0);
-    } else {
-      const int lo = q < opp(q) ? q : opp(q);
-      const __half* base = reinterpret_cast<const __half*>(a.srcq[lo]);
-      // a non-fluid cell reads through its own cell (as a boundary link)
-      const bool b0 = !f0 || ((e.y >> q) & 1u), b1 = !f1 || ((e.z >> q) & 1u);
-      const unsigned i0 = c0 + (b0 ? a.lb[q] : a.lf[q]);
-      const unsigned i1 = c0 + 1u + (b1 ? a.lb[q] : a.lf[q]);
-      if (L::cx(q) == 0 && b0 == b1) P[q] = pdf_ld<__half2>(a, base + i0, 0);
-      else P[q] = __halves2half2(pdf_ld<S>(a, base, i0), pdf_ld<S>(a, base, i1));
-    }
-  }
-  if (f0) {
-    T v[L::Q];
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
-    collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__float2half_rn(v[q]), __high2half(P[q]));
-  }
-  if (f1) {
-    T v[L::Q];
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
-    collide<L, T, true>(v, a.cp, std::integral_constant<int, OP>{});
-#pragma unroll
-    for (int q = 0; q < L::Q; ++q) P[q] = __halves2half2(__low2half(P[q]), __float2half_rn(v[q]));
-  }
-  // the entry again (a cache hit) rather than held across the collisions
-  uint4 es;
-  asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(es.x), "=r"(es.y), "=r"(es.z), "=r"(es.w)
-               : "l"(a.pairs + i));
-  const unsigned s0 = es.x;
-  const bool g0 = !(es.y & MASK_SOLID), g1 = !(es.z & MASK_SOLID);
-#pragma unroll
-  for (int q = 0; q < L::Q; ++q) {
-    if constexpr (KIND == K_PULL) {
-      pdf_st<__half2>(a, reinterpret_cast<__half*>(a.dstq[q]) + s0, 0, P[q]);
-    } else if constexpr (KIND == K_AA_EVEN) {
-      pdf_st<__half2>(a, reinterpret_cast<__half*>(a.dstq[opp(q)]) + s0, 0, P[q]);
-    } else {
-      const int p = opp(q);
-      const int lo = q < p ? q : p;
-      __half* base = reinterpret_cast<__half*>(a.dstq[lo]);
-      const bool b0 = (es.y >> p) & 1u, b1 = (es.z >> p) & 1u;
-      const unsigned i0 = s0 + (b0 ? a.sb[q] : a.sf[q]);
-      const unsigned i1 = s0 + 1u + (b1 ? a.sb[q] : a.sf[q]);
-      if (L::cx(q) == 0 && g0 && g1 && b0 == b1) {
-        pdf_st<__half2>(a, base + i0, 0, P[q]);
-      } else {
-        if (g0) pdf_st<S>(a, base, i0, __low2half(P[q]));
-        if (g1) pdf_st<S>(a, base, i1, __high2half(P[q]));
-      }
-    }
-  }
-  if constexpr (KIND != K_PULL) {
-    if (g0 && (es.y & MASK_SPECIAL)) {
-      T v[L::Q];
-#pragma unroll
-      for (int q = 0; q < L::Q; ++q) v[q] = __low2float(P[q]);
-      store_special_links<L, ST, true, KIND>(a, v, int(s0), es.y);
-    }
-    if (g1 && (es.z & MASK_SPECIAL)) {
-      T v[L::Q];
-#pragma unroll
-      for (int q = 0; q < L::Q; ++q) v[q] = __high2float(P[q]);
-      store_special_links<L, ST, true, KIND>(a, v, int(s0 + 1u), es.z);
-    }
-  }
 }
 
 template <class L, class ST, int OP, int KIND>
@@ -1660,24 +1481,7 @@ cudaError_t launch_sweep_k(bool bnd, const SweepArgs& a, cudaStream_t s) {
       k_sweep<L, ST, OP, KIND><<<sweep_grid(a.g), sweep_block(a.g), 0, s>>>(a);
     return cudaGetLastError();
   }
-  constexpr bool PAIRS = list_capped<L, ST, OP>() && KIND != K_ESO_EVEN && KIND != K_ESO_ODD;
-  if (PAIRS && a.pairs != nullptr) {
-    if constexpr (PAIRS) {
-      if (a.n_pairs > 0) {
-        static int resident = 0;
-        if (resident == 0) {
-          int dev = 0, sms = 0, per_sm = 0;
-          cudaGetDevice(&dev);
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pairs_h2<L, OP, KIND>, kBlockX, 0);
-          resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * kBlockX;
-        }
-        SweepArgs b = a;
-        b.list_ahead = resident + resident / 2;
-        k_sweep_pairs_h2<L, OP, KIND><<<(a.n_pairs + kBlockX - 1) / kBlockX, kBlockX, 0, s>>>(b);
-      }
-    }
-  } else if (a.n_main > 0) {
+  if (a.n_main > 0) {
     // entry prefetch distance: one and a half times the threads resident at
     // once (blocks per SM from the occupancy calculator, per instantiation)
     static int resident = 0;

@@ -118,18 +118,6 @@ cudaError_t launch_list_count(const SweepArgs& a, int nblk, int* counts, cudaStr
 }
 
 template <class L>
-cudaError_t launch_pair_count(const SweepArgs& a, int nblk, int* counts, cudaStream_t s) {
-  k_pair_count<L><<<nblk, kListThreads, 0, s>>>(a, nblk, counts);
-  return cudaGetLastError();
-}
-
-template <class L>
-cudaError_t launch_pair_scatter(const SweepArgs& a, int nblk, const int* offsets, uint4* pairs, cudaStream_t s) {
-  k_pair_scatter<L><<<nblk, kListThreads, 0, s>>>(a, nblk, offsets, pairs);
-  return cudaGetLastError();
-}
-
-template <class L>
 cudaError_t launch_list_scatter(const SweepArgs& a, int nblk, const int* offsets, uint2* list, cudaStream_t s) {
   k_list_scatter<L><<<nblk, kListThreads, 0, s>>>(a, nblk, offsets, list);
   return cudaGetLastError();
@@ -151,8 +139,6 @@ struct OpsTable {
   cudaError_t (*list_scatter)(const SweepArgs&, int, const int*, uint2*, cudaStream_t);
   cudaError_t (*boundary_pull)(const SweepArgs&, void*, cudaStream_t);
   cudaError_t (*halo)(const SweepArgs&, HaloSpec, void*, cudaStream_t);
-  cudaError_t (*pair_count)(const SweepArgs&, int, int*, cudaStream_t);
-  cudaError_t (*pair_scatter)(const SweepArgs&, int, const int*, uint4*, cudaStream_t);
 };
 
 template <class L, class ST>
@@ -161,7 +147,7 @@ OpsTable make_table() {
                   &Ops<L, ST>::reduce_partial, &Ops<L, ST>::set_state,   &launch_link_mask<L>,
                   &Ops<L, ST>::adjoint,        &Ops<L, ST>::ke_seed,     &Ops<L, ST>::eq_vjp,
                   &launch_list_count<L>,       &launch_list_scatter<L>,  &launch_boundary_pull<L, ST>,
-                  &launch_halo<L, ST>,         &launch_pair_count<L>,    &launch_pair_scatter<L>};
+                  &launch_halo<L, ST>};
 }
 
 #define LBM_TABLE_DECL(l, s) OpsTable ops_table_##l##_##s();

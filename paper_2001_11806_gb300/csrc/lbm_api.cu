@@ -322,6 +322,7 @@ SweepArgs make_args(const lbm_ctx* c, const void* src, void* dst) {
   a.boundary_mode = c->p.boundary_mode;
   a.special_wrap = (c->p.pattern == LBM_PULL && c->p.boundary_mode == LBM_BOUNDARY_IN_SWEEP) ? 1 : 0;
   a.list_ahead = 0;
+  a.pop_ahead = 0;
   a.pdf_bytes = c->pdf_bytes;
   a.bounds_flag = bounds_word(c);
   for (int q = 0; q < 27; ++q) {

@@ -81,10 +81,18 @@ struct lbm_ctx {
   // single-array patterns, which start a graph at even parity).
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // list sweeps with a second launch: the stream and events that run it
+  // beside the main launch (SideStream; s null when the list has no second
+  // part)
+  SideStream side = {nullptr, nullptr, nullptr};
+  const SideStream* side_or_null() const { return side.s ? &side : nullptr; }
   ~lbm_ctx() {
     for (auto& g : graph)
       if (g) cudaGraphExecDestroy(g);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side.join) cudaEventDestroy(side.join);
+    if (side.fork) cudaEventDestroy(side.fork);
+    if (side.s) cudaStreamDestroy(side.s);
   }
 };
 
@@ -399,13 +407,13 @@ cudaError_t sweep_once(lbm_ctx* c, cudaStream_t s, int64_t t, int cur) {
       const cudaError_t e = c->ops.boundary_pull(a, c->buf[cur], s);
       if (e != cudaSuccess) return e;
     }
-    return c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, s);
+    return c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, s, c->side_or_null());
   }
   SweepArgs a = make_args(c, c->buf[0], c->buf[0]);
   const bool odd = (t & 1) != 0;
   const int kind = c->p.pattern == LBM_AA ? (odd ? K_AA_ODD : K_AA_EVEN) : (odd ? K_ESO_ODD : K_ESO_EVEN);
   set_interior(a, c, kind);
-  return c->ops.sweep(c->kernel_op, kind, c->has_mask, a, s);
+  return c->ops.sweep(c->kernel_op, kind, c->has_mask, a, s, c->side_or_null());
 }
 
 // Records kGraphSteps sweeps starting from pull buffer g (or even parity)
@@ -591,6 +599,15 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_params* p, void* pdf, size_t pdf_
       delete c;
       return ls;
     }
+    if (c->n_main > 0 && c->n_wrap > 0) {
+      cudaError_t se = cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking);
+      if (se == cudaSuccess) se = cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming);
+      if (se == cudaSuccess) se = cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming);
+      if (se != cudaSuccess) {
+        delete c;
+        return LBM_E_CUDA;
+      }
+    }
   }
   *out = c;
   return LBM_OK;
@@ -734,7 +751,7 @@ lbm_status lbm_step_pull(lbm_ctx* c, const void* src, void* dst) {
   if (c->p.boundary_mode == LBM_BOUNDARY_SEPARATE) return LBM_E_UNSUPPORTED;
   SweepArgs a = make_args(c, src, dst);
   set_interior(a, c, K_PULL);
-  cudaError_t e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream);
+  cudaError_t e = c->ops.sweep(c->kernel_op, K_PULL, c->has_mask, a, c->stream, c->side_or_null());
   return e == cudaSuccess ? debug_check(c) : cuda_fail(c, e, "step_pull");
 }
 

@@ -10,17 +10,17 @@ namespace lbm {
 // one translation unit per pair.
 template <class L, class ST>
 struct Ops {
-  static cudaError_t sweep(int op, int kind, bool bnd, const SweepArgs& a, cudaStream_t s) {
+  static cudaError_t sweep(int op, int kind, bool bnd, const SweepArgs& a, cudaStream_t s, const SideStream* side) {
     switch (op) {
-      case OP_SRT: return launch_sweep_op<L, ST, OP_SRT>(kind, bnd, a, s);
-      case OP_TRT: return launch_sweep_op<L, ST, OP_TRT>(kind, bnd, a, s);
-      case OP_MRT: return launch_sweep_op<L, ST, OP_MRT>(kind, bnd, a, s);
-      case OP_SRT_LES: return launch_sweep_op<L, ST, OP_SRT_LES>(kind, bnd, a, s);
-      case OP_TRT_LES: return launch_sweep_op<L, ST, OP_TRT_LES>(kind, bnd, a, s);
-      case OP_KBC: return launch_sweep_op<L, ST, OP_KBC>(kind, bnd, a, s);
-      case OP_MRT3: return launch_sweep_op<L, ST, OP_MRT3>(kind, bnd, a, s);
+      case OP_SRT: return launch_sweep_op<L, ST, OP_SRT>(kind, bnd, a, s, side);
+      case OP_TRT: return launch_sweep_op<L, ST, OP_TRT>(kind, bnd, a, s, side);
+      case OP_MRT: return launch_sweep_op<L, ST, OP_MRT>(kind, bnd, a, s, side);
+      case OP_SRT_LES: return launch_sweep_op<L, ST, OP_SRT_LES>(kind, bnd, a, s, side);
+      case OP_TRT_LES: return launch_sweep_op<L, ST, OP_TRT_LES>(kind, bnd, a, s, side);
+      case OP_KBC: return launch_sweep_op<L, ST, OP_KBC>(kind, bnd, a, s, side);
+      case OP_MRT3: return launch_sweep_op<L, ST, OP_MRT3>(kind, bnd, a, s, side);
       case OP_CUM:
-        if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s);
+        if constexpr (L::Q == 27) return launch_sweep_op<L, ST, OP_CUM>(kind, bnd, a, s, side);
         return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
@@ -126,7 +126,7 @@ cudaError_t launch_list_scatter(const SweepArgs& a, int nblk, const int* offsets
 // Dispatch table of one (stencil, storage) pair.  Each lbm_inst_*.cu defines
 // one factory returning it, so the C ABI unit instantiates no kernels.
 struct OpsTable {
-  cudaError_t (*sweep)(int, int, bool, const SweepArgs&, cudaStream_t);
+  cudaError_t (*sweep)(int, int, bool, const SweepArgs&, cudaStream_t, const SideStream*);
   cudaError_t (*populations)(int, const SweepArgs&, double*, cudaStream_t);
   cudaError_t (*macroscopic)(int, const SweepArgs&, void*, void*, bool, cudaStream_t);
   cudaError_t (*reduce_partial)(int, const SweepArgs&, double*, int, cudaStream_t);

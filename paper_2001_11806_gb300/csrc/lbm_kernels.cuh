@@ -277,19 +277,25 @@ __device__ __forceinline__ void post_velocity(const T (&v)[L::Q], const OutletP&
 
 // Value of an inlet or outlet pull link (x, q) whose no-slip value v_noslip
 // = P_qbar(x) has already been loaded.  Rare path (cells next to an inlet or
-// outlet), so it is not inlined and takes scalars only.
+// outlet), so it is not inlined.  The outlet value needs u_P(x), the
+// velocity of the cell's P: the first outlet link of a cell loads and
+// reduces P(x) into up and sets have_up, and the cell's other outlet links
+// reuse it (the caller starts each cell with have_up = 0).
 template <class L, class ST, bool DH>
 __device__ __noinline__ typename ST::T pull_special(const typename ST::S* src, long long N, int cell, int q, int type,
-                                                    typename ST::T v_noslip, const OutletP p, double ubb) {
+                                                    typename ST::T v_noslip, const OutletP p, double ubb,
+                                                    typename ST::T (&up)[3], int& have_up) {
   using T = typename ST::T;
   if (type == L_INLET) return v_noslip + T(ubb);
   if (type != L_OUTLET) return v_noslip;
-  T v[L::Q];
+  if (!have_up) {
+    T v[L::Q];
 #pragma unroll
-  for (int k = 0; k < L::Q; ++k) v[k] = Dom<ST, DH>::load(src[k * N + cell], L::w(k));
-  T u[3];
-  post_velocity<L, T, DH>(v, p, u);
-  return outlet_value<L, T, DH>(q, u, p);
+    for (int k = 0; k < L::Q; ++k) v[k] = Dom<ST, DH>::load(src[k * N + cell], L::w(k));
+    post_velocity<L, T, DH>(v, p, up);
+    have_up = 1;
+  }
+  return outlet_value<L, T, DH>(q, up, p);
 }
 
 template <class L, class T, bool DH>
@@ -658,12 +664,15 @@ __device__ __forceinline__ void sweep_list(const SweepArgs& a, const uint2 entry
       int x, y, z;
       cell_coords(a.g, cell, x, y, z);
       const OutletP op = outlet_params(a.cp);
+      T up[3];
+      int have_up = 0;
       for (int q = 1; q < L::Q; ++q) {
         if ((mask >> q) & 1u) {
           const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
           const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
                                               L::cz(q) * a.cp.u_wall[2]);
-          v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb);
+          v[q] = pull_special<L, ST, DH>(static_cast<const S*>(a.src), a.g.N, cell, q, t, v[q], op, ubb, up,
+                                         have_up);
         }
       }
     }
@@ -1150,12 +1159,14 @@ __device__ void gather_h(const SweepArgs& a, int view, int x, int y, int z, int 
   }
   if (mask & MASK_SPECIAL) {
     const OutletP op = outlet_params(a.cp);
+    T up[3];
+    int have_up = 0;
     for (int q = 1; q < L::Q; ++q) {
       if ((mask >> q) & 1u) {
         const int t = LBM_LINK_TYPE(a, x - L::cx(q), y - L::cy(q), z - L::cz(q));
         const double ubb = 6.0 * L::w(q) * (L::cx(q) * a.cp.u_wall[0] + L::cy(q) * a.cp.u_wall[1] +
                                             L::cz(q) * a.cp.u_wall[2]);
-        h[q] = pull_special<L, ST, true>(A, N, cell, q, t, h[q], op, ubb);
+        h[q] = pull_special<L, ST, true>(A, N, cell, q, t, h[q], op, ubb, up, have_up);
       }
     }
   }
